@@ -1,0 +1,276 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+No GPU.  Each test checks the oracle against something other than itself:
+the explicit matrix A_n^h built by the recursion of Property 1, library
+routines (numpy/scipy convolution, correlation and NNLS), closed forms and
+invariants.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle.dense import dense_A
+
+SHAPES = [
+    ((7,), (3,)),
+    ((5,), (9,)),            # template larger than the signal (q > m)
+    ((1,), (5,)),
+    ((6,), (1,)),            # p = 0
+    ((4, 5), (3, 5)),
+    ((3, 2), (5, 3)),
+    ((3, 4, 5), (3, 1, 3)),
+    ((2, 3, 4), (3, 5, 3)),
+    ((4, 3, 2), (1, 3, 5)),
+]
+
+
+@pytest.mark.parametrize("m,q", SHAPES)
+def test_forward_equals_dense_A_exactly(m, q):
+    """Property 1 / Eq. 1: Y^v = A_n^h X^v, exact on integer data."""
+    X, H = synth.integer_case(m, q, seed=len(m) * 100 + sum(m) + sum(q))
+    A = dense_A(H, m)
+    Y = oracle.forward(X, H)
+    assert Y.shape == tuple(a + b - 1 for a, b in zip(m, q))
+    np.testing.assert_array_equal(Y.ravel(), A @ X.astype(np.float64).ravel())
+
+
+@pytest.mark.parametrize("m,q", SHAPES)
+def test_adjoint_equals_dense_transpose_exactly(m, q):
+    """Property 2 / Eq. 2: (A_n^h)^T R^v = {M_2p(R (*) H~)}^v, exact on integers."""
+    X, H = synth.integer_case(m, q, seed=7 + sum(m))
+    rng = np.random.default_rng(3)
+    R = rng.integers(-4, 5, size=tuple(a + b - 1 for a, b in zip(m, q))).astype(np.float64)
+    A = dense_A(H, m)
+    G = oracle.adjoint(R, H)
+    Gc = oracle.adjoint_crop(R, H)
+    assert G.shape == tuple(m)
+    np.testing.assert_array_equal(G.ravel(), A.T @ R.ravel())
+    np.testing.assert_array_equal(Gc, G)
+
+
+def test_extended_transpose_crop_offset():
+    """Eq. S9/S11: the full conv with H~ has m + 4p samples and its crop starts at 2p."""
+    m, q = (6,), (5,)
+    X, H = synth.integer_case(m, q, seed=11)
+    R = np.arange(1, 11, dtype=np.float64)
+    Ht = H[::-1].astype(np.float64)
+    full = np.convolve(R, Ht)          # textbook 1-D full convolution, m + 4p samples
+    assert full.shape[0] == 6 + 8
+    np.testing.assert_array_equal(oracle.adjoint(R, H), full[4:4 + 6])
+    # shifting the crop by one is wrong: pins the offset
+    assert not np.array_equal(oracle.adjoint(R, H), full[3:3 + 6])
+
+
+@pytest.mark.parametrize("m,q", [((9, 8), (3, 5)), ((5, 6, 7), (3, 3, 5)), ((33,), (7,))])
+def test_matches_scipy_convolve_and_correlate(m, q):
+    """Library routines: scipy.signal.convolve(full) and correlate(valid)."""
+    from scipy.signal import convolve, correlate
+    X, H, R = synth.random_case(m, q, seed=5)
+    np.testing.assert_allclose(oracle.forward(X, H),
+                               convolve(X.astype(np.float64), H.astype(np.float64), mode="full", method="direct"),
+                               rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(oracle.adjoint(R, H),
+                               correlate(R.astype(np.float64), H.astype(np.float64), mode="valid", method="direct"),
+                               rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("m,q", [((17, 12, 9), (5, 3, 7)), ((40, 31), (7, 9))])
+def test_adjoint_identity(m, q):
+    """<A x, r> = <x, A^T r> to FP64 rounding."""
+    X, H, R = synth.random_case(m, q, seed=9)
+    lhs = float(np.dot(oracle.forward(X, H).ravel(), R.astype(np.float64).ravel()))
+    rhs = float(np.dot(X.astype(np.float64).ravel(), oracle.adjoint(R, H).ravel()))
+    assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(lhs))
+
+
+def test_delta_templates_zero_boundary():
+    """Zero boundary, no wrap-around: delta at 0 puts X in the corner, delta at the centre at offset p."""
+    X, _ = synth.integer_case((5, 6, 4), (1, 1, 1), seed=1)
+    q = (3, 5, 3)
+    H0 = np.zeros(q); H0[0, 0, 0] = 1
+    Y0 = oracle.forward(X, H0)
+    exp0 = np.zeros(Y0.shape); exp0[:5, :6, :4] = X
+    np.testing.assert_array_equal(Y0, exp0)
+    Hc = np.zeros(q); Hc[1, 2, 1] = 1
+    Yc = oracle.forward(X, Hc)
+    expc = np.zeros(Yc.shape); expc[1:6, 2:8, 1:5] = X
+    np.testing.assert_array_equal(Yc, expc)
+    # adjoint of a centre delta is the centre crop
+    np.testing.assert_array_equal(oracle.adjoint(Yc, Hc), X)
+
+
+def test_convolution_not_correlation():
+    """h(s - k): a ramp template is applied flipped relative to correlation."""
+    X = np.zeros(5); X[2] = 1
+    H = np.array([1.0, 2.0, 3.0])
+    np.testing.assert_array_equal(oracle.forward(X, H), [0, 0, 1, 2, 3, 0, 0])
+    R = np.array([0, 0, 1.0, 0, 0, 0, 0])
+    np.testing.assert_array_equal(oracle.adjoint(R, H), [3, 2, 1, 0, 0])
+
+
+def test_commutativity_and_mass():
+    X, H = synth.integer_case((5, 7, 3), (3, 5, 9), seed=21)
+    np.testing.assert_array_equal(oracle.forward(X, H), oracle.forward(H, X))
+    Xr, Hr, _ = synth.random_case((11, 6, 9), (5, 3, 3), seed=2, positive=True)
+    Y = oracle.forward(Xr, Hr)
+    assert abs(Y.sum() - Xr.astype(np.float64).sum() * Hr.astype(np.float64).sum()) < 1e-11 * Y.sum()
+
+
+def test_separable_closed_form():
+    """Separable X and H: Y is the outer product of 1-D textbook convolutions."""
+    rng = np.random.default_rng(4)
+    a, b, c = rng.random(9), rng.random(7), rng.random(12)
+    H = synth.gaussian_psf((5, 7, 3), (1.2, 2.0, 0.9)).astype(np.float64)
+    u, v, w = H.sum(axis=(1, 2)), H.sum(axis=(0, 2)), H.sum(axis=(0, 1))
+    Hs = np.einsum("i,j,k->ijk", u, v, w)          # the Gaussian is separable: rebuild it as an outer product
+    np.testing.assert_allclose(Hs, H, rtol=1e-5, atol=1e-9)
+    X = np.einsum("i,j,k->ijk", a, b, c)
+    Y = oracle.forward(X, Hs)
+    Yc = np.einsum("i,j,k->ijk", np.convolve(a, u), np.convolve(b, v), np.convolve(c, w))
+    np.testing.assert_allclose(Y, Yc, rtol=1e-12, atol=1e-14)
+
+
+def test_points_match_full():
+    X, H, R = synth.random_case((13, 10, 17), (5, 7, 3), seed=8)
+    Y = oracle.forward(X, H)
+    G = oracle.adjoint(R, H)
+    rng = np.random.default_rng(0)
+    si = np.stack([rng.integers(0, n, 50) for n in Y.shape], axis=1)
+    ki = np.stack([rng.integers(0, n, 50) for n in G.shape], axis=1)
+    np.testing.assert_allclose(oracle.forward_points(X, H, si), Y[tuple(si.T)], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(oracle.adjoint_points(R, H, ki), G[tuple(ki.T)], rtol=1e-12, atol=1e-12)
+
+
+def test_grad_psf_finite_differences():
+    """dH of L = <X (*) H, W> against central differences in FP64 (h = 1e-3)."""
+    rng = np.random.default_rng(12)
+    B, m, q = 2, (5, 6, 4), (3, 3, 3)
+    X = rng.random((B,) + m)
+    H = rng.random(q)
+    W = rng.standard_normal((B,) + tuple(a + b - 1 for a, b in zip(m, q)))
+    dH = oracle.grad_psf(X, W, q)
+
+    def L(Hv):
+        return sum(float(np.sum(oracle.forward(X[b], Hv) * W[b])) for b in range(B))
+    fd = np.zeros(q)
+    for j in np.ndindex(q):
+        e = np.zeros(q); e[j] = 1e-3
+        fd[j] = (L(H + e) - L(H - e)) / 2e-3
+    np.testing.assert_allclose(dH, fd, rtol=1e-8, atol=1e-8)
+    # and against the library valid correlation of W with X
+    from scipy.signal import correlate
+    lib = sum(correlate(W[b], X[b], mode="valid", method="direct") for b in range(B))
+    np.testing.assert_allclose(dH, lib, rtol=1e-12, atol=1e-12)
+
+
+def test_grad_psf_dense_subcase():
+    """8x8x8 / 3x3x3: dX = A^T dY from the explicit matrix, dH by the dense matrix of the roles swapped."""
+    rng = np.random.default_rng(13)
+    X = rng.random((8, 8, 8))
+    H = rng.random((3, 3, 3))
+    dY = rng.standard_normal((10, 10, 10))
+    A = dense_A(H, (8, 8, 8))
+    np.testing.assert_allclose(oracle.adjoint(dY, H).ravel(), A.T @ dY.ravel(), rtol=1e-12, atol=1e-12)
+    # y is linear in h: y^v = B_X h^v with B_X[s, j] = x(s - j); dH = B_X^T dY^v
+    Bx = np.zeros((1000, 27))
+    for ji, j in enumerate(np.ndindex(3, 3, 3)):
+        e = np.zeros((3, 3, 3)); e[j] = 1.0
+        Bx[:, ji] = dense_A(e, (8, 8, 8)) @ X.ravel()
+    np.testing.assert_allclose(oracle.grad_psf(X[None], dY[None], (3, 3, 3)).ravel(), Bx.T @ dY.ravel(),
+                               rtol=1e-12, atol=1e-12)
+
+
+def test_eq6_literal_equals_residual_form():
+    P = synth.blobs2d()
+    X0 = oracle.x0_crop(P.Y, P.p)
+    lit, res = oracle.gradient_eq6(X0, P.H, P.Y)
+    assert np.linalg.norm(lit - res) <= 1e-12 * np.linalg.norm(res)
+
+
+def test_iterate_identity_template():
+    """H = delta (A = I): one step with delta = 1 reaches max(Y, 0), then the run is stationary."""
+    rng = np.random.default_rng(1)
+    Y = rng.standard_normal((6, 7))
+    H = np.ones((1, 1))
+    out = oracle.iterate(Y, H, np.zeros((6, 7)) + 0.5, K=5)
+    np.testing.assert_allclose(out["X"], np.maximum(Y, 0), rtol=0, atol=1e-15)
+    assert out["accepted"] == 1 and out["status"] == 1
+
+
+def test_iterate_monotone_and_nnls():
+    """Steps 1-3 decrease f every accepted step and converge to the library NNLS solution."""
+    from scipy.optimize import nnls
+    rng = np.random.default_rng(2)
+    H = synth.gaussian_psf((3, 3), (0.8, 0.8)).astype(np.float64)
+    Xt = np.maximum(rng.standard_normal((8, 8)), 0)
+    Y = oracle.forward(Xt, H) + 0.05 * rng.standard_normal((10, 10))
+    A = dense_A(H, (8, 8))
+    xs, _ = nnls(A, Y.ravel(), maxiter=5000)
+    out = oracle.iterate(Y, H, np.zeros((8, 8)), K=20000)
+    f = out["f"]
+    assert np.all(np.diff(f) < 0)
+    fs = 0.5 * np.sum((A @ xs - Y.ravel()) ** 2)
+    assert f[-1] - fs <= 1e-9 * max(fs, 1.0)
+    np.testing.assert_allclose(out["X"].ravel(), xs, atol=2e-3)
+    # KKT of the NNLS problem at the limit
+    g = A.T @ (A @ out["X"].ravel() - Y.ravel())
+    assert np.all(out["X"] >= 0)
+    assert np.all(g[out["X"].ravel() == 0] >= -1e-6)
+
+
+def test_iterate_fejer_monotone_noise_free():
+    """Noise-free Y from X_true > 0: ||x_k - X_true|| never grows with delta = 1/L."""
+    rng = np.random.default_rng(3)
+    H = synth.gaussian_psf((5, 3, 3), (1.0, 0.7, 0.7)).astype(np.float64)
+    Xt = rng.random((6, 5, 7)) + 0.1
+    Y = oracle.forward(Xt, H)
+    x = np.zeros_like(Xt)
+    d = [np.linalg.norm(x - Xt)]
+    for _ in range(30):
+        x = oracle.iterate(Y, H, x, K=1)["X"]
+        d.append(np.linalg.norm(x - Xt))
+    assert np.all(np.diff(d) <= 1e-12)
+    assert d[-1] < d[0]
+
+
+def test_iterate_backtracking():
+    """A too-long delta0 is halved until f decreases; accepted deltas are delta0 * beta^i."""
+    P = synth.blobs2d()
+    X0 = oracle.x0_crop(P.Y, P.p)
+    d0 = 8.0 / oracle.lipschitz(P.H)
+    out = oracle.iterate(P.Y, P.H, X0, K=10, delta0=d0, beta=0.5)
+    assert out["accepted"] == 10
+    assert out["rejected"] > 0
+    assert np.all(np.diff(out["f"]) < 0)
+    ratio = np.log2(d0 / out["delta"])
+    np.testing.assert_allclose(ratio, np.round(ratio), atol=1e-12)
+
+
+def test_iterate_matches_step_by_step():
+    """Two runs of K1 and K - K1 steps equal one run of K steps (state is x alone at fixed delta0)."""
+    P = synth.blobs2d()
+    X0 = oracle.x0_crop(P.Y, P.p)
+    a = oracle.iterate(P.Y, P.H, X0, K=7)
+    b1 = oracle.iterate(P.Y, P.H, X0, K=3)
+    b2 = oracle.iterate(P.Y, P.H, b1["X"], K=4)
+    np.testing.assert_array_equal(a["X"], b2["X"])
+    np.testing.assert_array_equal(a["f"][3:], b2["f"])
+
+
+def test_richardson_lucy_flux_and_fixed_point():
+    """RL keeps sum(x) * sum(h) = sum(y), and y = A x_true is a fixed point at x_true."""
+    rng = np.random.default_rng(5)
+    H = synth.gaussian_psf((5, 5), (1.2, 1.2)).astype(np.float64)
+    Xt = rng.random((9, 10)) + 0.2
+    Y = oracle.forward(Xt, H)
+    np.testing.assert_allclose(oracle.richardson_lucy(Y, H, Xt, 3), Xt, rtol=1e-12)
+    Yn = Y + 0.01 * rng.random(Y.shape)
+    x = oracle.richardson_lucy(Yn, H, np.ones_like(Xt), 4)
+    assert abs(x.sum() * H.sum() - Yn.sum()) < 1e-10 * Yn.sum()
+
+
+def test_lipschitz_bounds_operator_norm():
+    H = synth.ring_psf(q=(7, 7, 5), sigma=(1, 1, 1.5), ring_r=2.5, ring_w=0.7, ring_sz=1.0)
+    A = dense_A(H, (4, 5, 3))
+    assert np.linalg.norm(A, 2) ** 2 <= oracle.lipschitz(H) * (1 + 1e-12)
