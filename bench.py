@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Benchmark of the projected-gradient deconvolution hot path.
+
+Workload (default ``ring3d``): X 512x512x128 filaments, H 31x31x21
+Gaussian-plus-ring template, Y = X (*) H with Poisson noise.  One step is one
+accepted iteration of Steps 1-3: the adjoint convolution with the projected
+update, the forward convolution with the residual, and the FP64 decision on
+the device.  The timed region is one ``cdv_iterate`` call of K steps (a CUDA
+graph replay; it also runs the initial forward convolution of x_0).
+
+Metric: GMAC/s = algorithmic multiply-adds (convolutions executed x
+prod(m) x prod(2p+1)) / device time; iterations/s is reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cdv|reference]
+Under torchrun each rank solves its own copy of the workload (weak scaling);
+rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.55
+
+WORKLOADS = {
+    "ring3d": "X 512x512x128 filaments (320), H 31x31x21 Gaussian-plus-ring, Y = X (*) H + Poisson noise",
+    "fil3d": "X 256x256x64 filaments (40) + background 10, H 15x15x11 Gaussian sigma (1.5,1.5,3), Poisson noise",
+    "blobs2d": "X 64x64 Gaussian blobs (20), H 7x7 Gaussian sigma 1.5, Gaussian noise 0.01",
+}
+METRIC = "GMAC/s of projected-gradient deconvolution (forward + adjoint direct convolution per iteration)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cdv", choices=["cdv", "reference"])
+    ap.add_argument("--workload", default="ring3d", choices=sorted(WORKLOADS))
+    ap.add_argument("--mode", default="fp32", choices=["fp32", "bf16", "tf32", "split3"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sample-planes", type=int, default=96)
+    return ap.parse_args()
+
+
+def problem(name):
+    import synth
+    return {"ring3d": synth.ring3d, "fil3d": synth.fil3d, "blobs2d": synth.blobs2d}[name]()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_sample(P, planes):
+    """Time the FP64 oracle on a slab of the workload: forward + residual + adjoint + update."""
+    import oracle
+    m1 = min(planes, P.m[0]) if len(P.m) == 3 else P.m[0]
+    X = np.ascontiguousarray(P.X_true[:m1]).astype(np.float64)
+    Ys = oracle.forward(X[:1], P.H)          # touch the library (build/load) outside the clock
+    del Ys
+    Y = np.ascontiguousarray(P.Y[:m1 + P.H.shape[0] - 1]).astype(np.float64)
+    t0 = time.perf_counter()
+    R = oracle.forward(X, P.H) - Y
+    G = oracle.adjoint(R, P.H)
+    Xn = np.maximum(X - G, 0.0)
+    dt = time.perf_counter() - t0
+    del Xn
+    mac = 2.0 * X.size * P.H.size
+    return {"seconds": dt, "gmac": mac / 1e9, "planes": m1, "threads": oracle.num_threads()}
+
+
+def cpu_baseline(P, planes):
+    s = oracle_sample(P, planes)
+    nxnh = float(np.prod(P.m)) * float(P.H.size)
+    rate = s["gmac"] / s["seconds"]
+    return {"value": rate, "unit": "GMAC/s", "cores": s["threads"], "kind": "oracle",
+            "iters_per_s": rate * 1e9 / (2.0 * nxnh),
+            "sample": "FP64 oracle forward + residual + adjoint + update on planes [0, %d) of axis 1 "
+                      "(%.3g GMAC, %.1f s)" % (s["planes"], s["gmac"], s["seconds"])}
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.p is None:
+            return
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        for line in out.strip().splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) >= 8:
+                self.rows.append(f)
+
+    def summary(self):
+        rows = getattr(self, "rows", [])
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[0]) for r in rows if num(r[0]) is not None]
+        mx = [num(r[1]) for r in rows if num(r[1]) is not None]
+        pw = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- GPU arm
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("conv_fp32.cuh",):
+        h.update(open(os.path.join(ROOT, "paper_1711_11224_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_record(workload, kernel):
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))
+        e = rec[workload][kernel]
+        if e.get("source_hash") != kernel_hash():
+            return None
+        return float(e["bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def time_kernel(fn, stream, reps=3):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / reps / 1e3
+
+
+def run_cdv(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
+    from paper_1711_11224_gb300 import Plan
+    P = problem(args.workload)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    Y = torch.from_numpy(P.Y).to(dev)
+    H = torch.from_numpy(P.H).to(dev)
+    X = torch.empty(P.m, device=dev, dtype=torch.float32)
+    pl = Plan(P.m, P.p, mode=args.mode)
+    pl.set_psf(H)
+    K = args.steps
+    nxnh = float(np.prod(P.m)) * float(P.H.size)
+
+    # warm-up: at least W steps, and the K-step graph captured outside the clock
+    done = 0
+    while True:
+        _, rep = pl.iterate(Y, X, K=K, x0="crop")
+        done += K
+        if done >= args.warmup:
+            break
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        _, rep = pl.iterate(Y, X, K=K, x0="crop")
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t = ev0.elapsed_time(ev1) / 1e3
+    if dist:
+        tt = torch.tensor([t], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    gmac_rank = rep["gmac"]
+    value = gmac_rank * ws / t
+    iters = rep["accepted"] * ws / t
+    launches = 1 + 1 + 1 + 1 + 3 * (K + 16) + 1   # x0, state, initial forward, initial decide, slots, finalize
+
+    out = {"metric": METRIC, "value": value, "unit": "GMAC/s", "n_gpus": ws, "steps": K, "warmup": args.warmup,
+           "ms_per_step": t * 1e3 / max(1, rep["accepted"]), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32" if args.mode == "fp32" else args.mode, "data": "synthetic",
+           "config": {"workload": "%s: %s" % (args.workload, WORKLOADS[args.workload]), "mode": args.mode,
+                      "K_per_call": K, "accepted": rep["accepted"], "rejected": rep["rejected"],
+                      "status": rep["status"], "parallelism": "independent problem per GPU" if ws > 1 else "1 GPU",
+                      "l2": "inputs larger than L2 (Y %.0f MB, X %.0f MB > 129 MB)"
+                            % (P.Y.nbytes / 1e6, P.X_true.nbytes / 1e6)},
+           "iters_per_s": iters, "gpu_launches": launches}
+
+    # per-kernel timing of the two convolutions (CUDA events on the launching stream)
+    R = torch.empty(P.Y.shape, device=dev, dtype=torch.float32)
+    G = torch.empty(P.m, device=dev, dtype=torch.float32)
+    Xs = X.clone()
+    tf = time_kernel(lambda: pl.forward(Xs, R), stream)
+    ta = time_kernel(lambda: pl.adjoint(R, G), stream)
+    flops = 2.0 * nxnh
+    dom, tdom = ("forward", tf) if tf >= ta else ("adjoint", ta)
+    achieved = flops / tdom / 1e12
+    traffic = traffic_record(args.workload, dom)
+    out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                       "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic, "kernel": "conv_fp32 " + dom,
+                       "forward_ms": tf * 1e3, "adjoint_ms": ta * 1e3,
+                       "forward_frac": flops / tf / 1e12 / FP32_PEAK_TFLOPS,
+                       "adjoint_frac": flops / ta / 1e12 / FP32_PEAK_TFLOPS,
+                       "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (FFMA)"}
+    out["clocks"] = clk.summary()
+
+    # end to end through the host-array C-ABI call (pinned buffers, copies inside the clock)
+    if not args.no_e2e:
+        Yh = torch.empty(P.Y.shape, dtype=torch.float32, pin_memory=True)
+        Yh.copy_(torch.from_numpy(P.Y))
+        Xh = torch.empty(P.m, dtype=torch.float32, pin_memory=True)
+        Yn, Xn = Yh.numpy(), Xh.numpy()
+        pl.iterate_host(Yn, Xn, K=K, x0="crop", report=False)    # capture its graph outside the clock
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        _, rep2 = pl.iterate_host(Yn, Xn, K=K, x0="crop")
+        te = time.perf_counter() - t0
+        if dist:
+            tt = torch.tensor([te], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        out["e2e"] = {"value": rep2["gmac"] * ws / te, "unit": "GMAC/s",
+                      "h2d_bytes_per_step": int(P.Y.nbytes), "d2h_bytes_per_step": int(P.X_true.nbytes),
+                      "seconds": te, "call": "cdv_iterate_host (x0 = centre crop of Y; K steps per call)"}
+    if rank == 0 and not args.no_cpu and ws == 1:
+        out["cpu_baseline"] = cpu_baseline(P, args.cpu_sample_planes)
+    pl.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- reference arm (FP64 oracle)
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    P = problem(args.workload)
+    planes = max(1, args.cpu_sample_planes // 2)
+    for _ in range(args.warmup):
+        oracle_sample(P, max(1, planes // 8))
+    tot_s = tot_g = 0.0
+    thr = 1
+    for _ in range(args.steps):
+        s = oracle_sample(P, planes)
+        tot_s += s["seconds"]
+        tot_g += s["gmac"]
+        thr = s["threads"]
+    rate = tot_g / tot_s
+    nxnh = float(np.prod(P.m)) * float(P.H.size)
+    out = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "GMAC/s", "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_s * 1e3 / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "%s: %s" % (args.workload, WORKLOADS[args.workload]), "mode": "oracle"},
+           "iters_per_s": rate * 1e9 / (2.0 * nxnh),
+           "cpu_baseline": {"value": rate, "unit": "GMAC/s", "cores": thr, "kind": "oracle",
+                            "sample": "each step: FP64 oracle forward + residual + adjoint + update on planes "
+                                      "[0, %d) of axis 1 of the workload" % planes},
+           "e2e": {"value": rate, "unit": "GMAC/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_cdv(args)
+
+
+if __name__ == "__main__":
+    main()

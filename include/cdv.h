@@ -1,0 +1,196 @@
+/*
+ * cdv -- direct-convolution deconvolution on GB300 (sm_103a).
+ *
+ * C ABI of the hot path of "Properties on n-dimensional convolution for image
+ * deconvolution" (arXiv 1711.11224): the full n-D convolution Y = X (*) H
+ * (Property 1, Eq. 1), its adjoint (A_n^h)^T R = M_2p(R (*) H~) (Property 2,
+ * Eq. 2), and the projected-gradient non-negative least-squares iteration
+ * built from the two (Steps 1-3 and Eq. 6 of the 2-D application, applied to
+ * n = 1, 2, 3).
+ *
+ * Notation follows the paper: X has m_i samples per axis, the template H has
+ * q_i = 2 p_i + 1, Y and every residual R have m_i + 2 p_i.  Arrays are dense
+ * C-order float32 (axis 1 slowest, axis n contiguous: the row partition of the
+ * vectorisation X^v), in DEVICE memory unless a name ends in _host.
+ *
+ * Conventions for every call:
+ *  - The caller owns every array it passes; the library never frees them.
+ *    A plan owns its copy of H, the flipped template and a workspace, all
+ *    allocated by cdv_plan_create / cdv_plan_set_psf and freed by
+ *    cdv_plan_destroy.  cdv_forward, cdv_adjoint and cdv_iterate allocate
+ *    nothing.
+ *  - `stream` is a cudaStream_t passed as void* (NULL: the legacy default
+ *    stream).  Work is enqueued asynchronously on it unless a call says it
+ *    synchronises.
+ *  - Argument errors return before anything is enqueued.  CUDA launch errors
+ *    return CDV_ERR_CUDA.  Errors raised on the device (non-finite values, a
+ *    wait that timed out) are recorded in the plan's device status word and
+ *    returned by cdv_plan_sync_status.
+ *  - A plan is not thread-safe: one host thread at a time per plan.
+ *  - There is no CPU fallback: without a usable CUDA device every call that
+ *    computes returns CDV_ERR_CUDA.
+ */
+#ifndef CDV_H
+#define CDV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CDV_OK = 0,
+    CDV_ERR_INVALID_ARG = 1,    /* null pointer, bad enum, K < 0, ... */
+    CDV_ERR_SHAPE = 2,          /* n not in {1,2,3}, m_i < 1, p_i < 0, sizes overflow */
+    CDV_ERR_UNSUPPORTED = 3,    /* a size or mode this build has no kernel for */
+    CDV_ERR_OOM = 4,            /* workspace allocation failed */
+    CDV_ERR_CUDA = 5,           /* a CUDA runtime call failed */
+    CDV_ERR_TIMEOUT = 6,        /* a bounded device-side wait ran out */
+    CDV_ERR_NOT_DESCENDING = 7, /* the step rule found no decreasing step */
+    CDV_ERR_NONFINITE = 8,      /* NaN/Inf met in the objective */
+    CDV_ERR_NO_PSF = 9          /* cdv_plan_set_psf was not called */
+} cdv_status;
+
+/* Arithmetic of the two convolutions (the iteration's scalars are FP64 in
+ * every mode). */
+typedef enum {
+    CDV_MODE_FP32 = 0,          /* FP32 FMA on CUDA cores */
+    CDV_MODE_BF16 = 1,          /* tensor cores, BF16 products, FP32 accumulate */
+    CDV_MODE_TF32 = 2,          /* tensor cores, TF32 products, FP32 accumulate */
+    CDV_MODE_SPLIT_BF16X3 = 3   /* tensor cores, x_hi h_hi + x_hi h_lo + x_lo h_hi */
+} cdv_mode;
+
+typedef struct cdv_plan cdv_plan;
+
+/* Human-readable name of a status code (static string). */
+const char* cdv_status_string(cdv_status s);
+
+/* Details of the last error raised on the calling host thread ("" if none). */
+const char* cdv_last_error(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int cdv_version(void);
+
+/*
+ * Plan for one problem size.  n in {1,2,3}; m[0..n-1] >= 1 samples of X per
+ * axis; p[0..n-1] >= 0 half-widths of H (H has 2p_i+1 samples per axis).
+ * Allocates the workspace on the current CUDA device (the plan is bound to
+ * it).  *out receives the plan, or NULL on error.
+ */
+cdv_status cdv_plan_create(cdv_plan** out, int n, const int64_t* m, const int32_t* p,
+                           cdv_mode mode, void* stream);
+
+/* Bytes of device memory the plan holds (workspace + templates). */
+cdv_status cdv_plan_workspace_size(const cdv_plan* plan, size_t* bytes);
+
+/*
+ * Set the template H (device, float32, C-order, prod(2p_i+1) values).  The
+ * plan copies it and derives, on `stream`, the flipped template
+ * H~(j) = h(2p - j) of Property 2 and sum_j |h(j)|, from which the default
+ * step length 1/L with L = (sum_j |h(j)|)^2 >= ||A||_2^2 is taken on the
+ * device.  Asynchronous; H may be reused by the caller once `stream` has
+ * reached this point.
+ */
+cdv_status cdv_plan_set_psf(cdv_plan* plan, const float* H, void* stream);
+
+/* Lipschitz bound L = (sum |h|)^2 of the current template (host value).
+ * Synchronises the device. */
+cdv_status cdv_plan_lipschitz(const cdv_plan* plan, double* L);
+
+/* Free everything the plan owns.  NULL is accepted. */
+cdv_status cdv_plan_destroy(cdv_plan* plan);
+
+/*
+ * Forward operator, Property 1 (Eq. 1): Y^v = A_n^h X^v, i.e.
+ * y(s) = sum_k x(k) h(s - k) with zeros outside X.  X: m, Y: m + 2p.
+ * `batch` volumes laid out back to back (X: batch*prod(m), Y: batch*prod(m+2p)).
+ */
+cdv_status cdv_forward(cdv_plan* plan, int batch, const float* X, float* Y, void* stream);
+
+/*
+ * Adjoint operator, Property 2 (Eq. 2): G^v = (A_n^h)^T R^v = {M_2p(R (*) H~)}^v,
+ * i.e. g(k) = sum_{j in [0,2p]} h(j) r(k + j).  R: m + 2p, G: m, `batch` volumes.
+ */
+cdv_status cdv_adjoint(cdv_plan* plan, int batch, const float* R, float* G, void* stream);
+
+/*
+ * Gradient of a loss L(Y) with Y = X (*) H with respect to H:
+ * dH(j) = sum_b sum_k X_b(k) dY_b(k + j)  (the adjoint sum of Property 2 with
+ * the roles of x and h exchanged).  X: batch*prod(m), dY: batch*prod(m+2p),
+ * dH: prod(2p+1), overwritten.  Uses the plan's workspace for block partials;
+ * the final sum is FP64 in a fixed order (deterministic).
+ */
+cdv_status cdv_grad_psf(cdv_plan* plan, int batch, const float* X, const float* dY, float* dH,
+                        void* stream);
+
+/* Initial solution of Step 1 (the paper leaves it open). */
+typedef enum {
+    CDV_X0_GIVEN = 0,   /* X holds x_0 on entry */
+    CDV_X0_CROP = 1,    /* x_0 = max(Y[p : p + m], 0), the centre crop of Y */
+    CDV_X0_ZERO = 2     /* x_0 = 0 */
+} cdv_x0_policy;
+
+typedef struct {
+    int x0_policy;      /* cdv_x0_policy, default CDV_X0_GIVEN */
+    double delta0;      /* step length tried first at every step; <= 0: 1/L (default) */
+    double beta;        /* factor applied to delta after a rejected trial, default 0.5 */
+    int max_halvings;   /* rejected trials allowed within one step, default 20 */
+    int max_rejects;    /* rejected trials allowed in the whole run, default 16 */
+    int use_graph;      /* 1: replay the captured K-step sequence as a CUDA graph (default) */
+    int reserved[4];
+} cdv_iter_opts;
+
+/* Fill `o` with the defaults above. */
+void cdv_iter_opts_default(cdv_iter_opts* o);
+
+typedef struct {
+    int accepted;       /* steps accepted (K unless stopped early) */
+    int rejected;       /* trials rejected by the decrease rule */
+    int status;         /* cdv_status of the run: CDV_OK, CDV_ERR_NOT_DESCENDING
+                           (converged: no decreasing step), CDV_ERR_NONFINITE */
+    int trials;         /* forward convolutions run after the initial one */
+    double f0;          /* f(x_0) = 1/2 ||A x_0 - y||^2 */
+    double f_final;     /* f at the last accepted iterate */
+    double gmac;        /* algorithmic multiply-adds executed, in units of 1e9 */
+    double* f_hist;     /* optional host array of K+1: f(x_0), ..., f(x_accepted) */
+    double* delta_hist; /* optional host array of K: accepted step lengths */
+} cdv_iter_report;
+
+/*
+ * Projected gradient of Steps 1-3:
+ *   x_{k+1} = max(x_k - delta_k A^T (A x_k - y), 0)
+ * (the residual form of Eq. 6), for K accepted steps, with delta_k the first
+ * of delta0, delta0*beta, delta0*beta^2, ... that makes f(x_{k+1}) < f(x_k).
+ * Every decision is taken on the device (FP64 objective), so the whole run is
+ * one CUDA-graph replay with no host round trip.
+ * Y: m + 2p (device), X: m (device; x_0 in per policy, x_K out).
+ * If `rep` is not NULL the call synchronises `stream` and fills it.
+ */
+cdv_status cdv_iterate(cdv_plan* plan, const float* Y, float* X, int K, const cdv_iter_opts* opts,
+                       cdv_iter_report* rep, void* stream);
+
+/*
+ * cdv_iterate with HOST arrays: copies Y_host (and X_host when the policy is
+ * CDV_X0_GIVEN) to the plan's device buffers, iterates, copies x_K back to
+ * X_host, and synchronises.  Pinned host memory gives the fastest copies.
+ */
+cdv_status cdv_iterate_host(cdv_plan* plan, const float* Y_host, float* X_host, int K,
+                            const cdv_iter_opts* opts, cdv_iter_report* rep, void* stream);
+
+/*
+ * Richardson-Lucy, the comparison method of the Results section:
+ *   x_{k+1} = x_k * A^T(y / A x_k) / A^T 1   (0 where A x_k = 0 or A^T 1 = 0).
+ * X holds x_0 > 0 on entry and x_K on return.  Asynchronous.
+ */
+cdv_status cdv_richardson_lucy(cdv_plan* plan, const float* Y, float* X, int K, void* stream);
+
+/* Wait for `stream`, then return and clear the plan's device status word. */
+cdv_status cdv_plan_sync_status(cdv_plan* plan, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CDV_H */

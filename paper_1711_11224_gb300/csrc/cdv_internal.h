@@ -1,0 +1,115 @@
+// Internal declarations shared by the CUDA translation units of libcdv.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cdv.h"
+
+namespace cdv {
+
+// What a convolution launch computes around the sum
+//   out[s] = sum_j w[j] * in[s + o - j]
+// (forward: in = X, o = 0, w = H; adjoint: in = R, o = 2p, w = H~).
+enum Role : int {
+    ROLE_PLAIN = 0,      // out = sum
+    ROLE_FWD_INIT = 1,   // r[cur] = A x[cur] - y, FP64 partials of ||r||^2
+    ROLE_FWD_TRIAL = 2,  // r[cur^1] = A x[cur^1] - y, FP64 partials of ||r||^2
+    ROLE_ADJ_TRIAL = 3,  // g = A^T r[cur] (unless reusing g), x[cur^1] = max(x[cur] - delta g, 0),
+                         // FP64 partials of ||x[cur^1] - x[cur]||^2
+    ROLE_RL_RATIO = 4,   // out = y / sum (0 where sum == 0)           (Richardson-Lucy)
+    ROLE_RL_UPDATE = 5,  // x = x * sum / norm (0 where norm == 0)     (Richardson-Lucy)
+};
+
+// Device-resident scalars of the projected-gradient iteration (FP64).
+struct IterState {
+    double f_cur;        // f(x_k)
+    double f_trial;      // f of the last trial
+    double delta;        // step length of the next trial
+    double delta0, beta;
+    double moved;        // ||x_trial - x_k||^2 of the last trial
+    int accepted, rejected, halvings, max_halvings;
+    int max_rejects, K, cur, need_grad;
+    int done, status, trials, hist_cap;
+    int adj_convs, pad_;
+};
+
+struct IterCtx {
+    float* x[2];         // x[0]: caller's X, x[1]: workspace
+    float* r[2];         // residual buffers (size of Y)
+    float* g;            // gradient A^T r (size of X)
+    const float* y;      // observation
+    const float* aux;    // Richardson-Lucy: A^T 1
+    double* part_f;      // per-CTA partials of ||r||^2
+    double* part_m;      // per-CTA partials of ||x_trial - x||^2
+    IterState* st;
+    double* f_hist;      // hist_cap + 1 entries
+    double* d_hist;      // hist_cap entries
+};
+
+// Geometry of one convolution, always 3-D (leading axes of size 1 for n < 3).
+struct ConvGeom {
+    int64_t a1, a2, a3;  // input dims
+    int64_t b1, b2, b3;  // output dims
+    int o1, o2, o3;      // offsets (0 forward, 2p adjoint)
+    int q1, q2, q3;      // template dims
+};
+
+struct ConvLaunch {
+    ConvGeom g;
+    const float* in;
+    float* out;
+    const float* w;      // q1*q2*q3 weights in C-order
+    const float* y;      // ROLE_RL_RATIO: observation
+    int role;
+    int batch;
+    int64_t in_bstride, out_bstride;
+    IterCtx ctx;
+};
+
+// Tile shape of the FP32 engine chosen for one geometry.
+struct ConvTile {
+    int ntx, nty;        // threads along axis 3 and axis 2
+    int tiles1, tiles2, tiles3;
+    int grid;            // CTAs per volume
+    size_t smem;         // dynamic shared memory bytes
+};
+
+// FP32 direct-convolution engine (CUDA cores).
+bool conv_fp32_supported(int q3);
+ConvTile conv_fp32_tile(const ConvGeom& g);
+cudaError_t conv_fp32_launch(const ConvLaunch& L, const ConvTile& t, cudaStream_t s);
+cudaError_t conv_fp32_prepare(int q3);   // once per process and width, outside stream capture
+cudaError_t grad_psf_prepare();
+
+// Per-Q3 launchers (one translation unit per group of template widths).
+template <int Q3>
+cudaError_t conv_fp32_launch_q(const ConvLaunch& L, const ConvTile& t, cudaStream_t s);
+
+// Iteration kernels (iterate.cu).
+cudaError_t launch_x0(int policy, float* x, const float* y, int64_t m1, int64_t m2, int64_t m3,
+                      int p1, int p2, int p3, cudaStream_t s);
+cudaError_t launch_state_init(IterState* st, double delta0, const double* absum, double beta, int max_halvings,
+                              int max_rejects, int K, int hist_cap, cudaStream_t s);
+cudaError_t launch_decide(const IterCtx& c, int nparts_f, int nparts_m, int init, cudaStream_t s);
+cudaError_t launch_finalize(const IterCtx& c, int64_t nx, cudaStream_t s);
+
+// Template preparation (psf.cu).
+cudaError_t launch_flip(const float* h, float* ht, int q1, int q2, int q3, cudaStream_t s);
+cudaError_t launch_abs_sum(const float* h, int64_t n, double* out, cudaStream_t s);
+
+// Template gradient (grad_psf.cu).
+struct GradPsfPlan {
+    int64_t m1, m2, m3;
+    int q1, q2, q3;
+    int batch;
+    int chunks;          // slabs of axis 1 reduced separately
+};
+size_t grad_psf_partials(const GradPsfPlan& g);
+cudaError_t launch_grad_psf(const GradPsfPlan& g, const float* X, const float* dY, double* partial,
+                            float* dH, cudaStream_t s);
+
+// Elementwise helpers (iterate.cu).
+cudaError_t launch_fill(float* x, int64_t n, float v, cudaStream_t s);
+
+}  // namespace cdv

@@ -1,0 +1,316 @@
+// FP32 direct-convolution engine on the CUDA cores.
+//
+// Computes, for every output sample s of a 3-D box,
+//     out[s] = sum_{j in [0,q)} w[j] * in[s + o - j]      (in = 0 outside its box)
+// which is the forward operator of Property 1 (in = X, o = 0, w = H, output
+// m + 2p) and the adjoint of Property 2 (in = R, o = 2p, w = H~, output m).
+//
+// Work decomposition (one CTA per output tile of T1 planes x nty rows x
+// ntx*R3 columns; one thread per row and R3 consecutive columns, all T1
+// planes):
+//  * The CTA streams the input planes u that reach its output planes.  Plane
+//    u's halo tile ((nty + q2 - 1) rows x pitch columns) and the T1 template
+//    planes j1 = s1 + o1 - u it meets are staged in shared memory with
+//    cp.async, double buffered, zero-filled outside the input box.
+//  * For each template row j2 a thread loads its input window of R3+Q3-1
+//    values into registers (16-byte shared loads) and slides it against the
+//    Q3 taps of every valid output plane (R3*Q3 FFMA per window per plane).
+//  * Two-level summation: the taps of one input plane are summed into a
+//    per-plane partial that is then added to the running total.  A single
+//    FP32 accumulator over all q1*q2*q3 taps loses the small terms of wide
+//    templates (about 1e-5 relative at 31x31x21); per-plane partials keep
+//    the error near 1e-7.
+//  * Output rows whose input rows fall outside the box skip those template
+//    rows (exact skipping along axes 1 and 2; along axis 3 the window is
+//    zero-padded).
+//  * Epilogues fuse the residual, the projected update, Richardson-Lucy
+//    ratios and the FP64 block partials of the iteration's norms.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cdv_internal.h"
+
+namespace cdv {
+
+constexpr int kR3 = 8;        // outputs per thread along the contiguous axis
+constexpr int kT1 = 4;        // output planes per CTA (and per thread)
+constexpr int kMaxThreads = 320;
+
+__host__ __device__ constexpr int ceil4(int v) { return (v + 3) & ~3; }
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool pred)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const int sz = pred ? 4 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(sz) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Block-wide FP64 sum; every thread passes its value, thread 0 gets the total.
+__device__ __forceinline__ double block_sum_f64(double v, double* s_red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) s_red[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < nw; i++) t += s_red[i];
+    return t;
+}
+
+// Shared-memory layout of one CTA (in floats).
+struct ConvSmem {
+    int rows, pitch, tile_in, tile_w;
+    __host__ __device__ static ConvSmem make(int ntx, int nty, int q2, int q3)
+    {
+        ConvSmem s;
+        s.rows = nty + q2 - 1;
+        s.pitch = ceil4((ntx - 1) * kR3 + ceil4(kR3 + q3 - 1));
+        s.tile_in = s.rows * s.pitch;
+        s.tile_w = kT1 * q2 * ceil4(q3);
+        return s;
+    }
+    __host__ __device__ size_t bytes() const
+    {
+        size_t f = 2 * (size_t)tile_in + 2 * (size_t)tile_w;
+        f = (f + 1) & ~(size_t)1;                       // 8-byte align the FP64 scratch
+        return f * sizeof(float) + 32 * sizeof(double);
+    }
+};
+
+template <int Q3>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+conv_fp32_kernel(const ConvLaunch L, const int ntx, const int nty, const int tiles2, const int tiles3)
+{
+    constexpr int R3 = kR3, T1 = kT1;
+    constexpr int WLP = ceil4(R3 + Q3 - 1);
+    constexpr int Q3P = ceil4(Q3);
+    extern __shared__ __align__(16) float smem[];
+
+    const ConvGeom& G = L.g;
+    const int tid = threadIdx.x;
+    const int tx = tid % ntx, ty = tid / ntx;
+    const int nthr = ntx * nty;
+    const int q1 = G.q1, q2 = G.q2;
+    const ConvSmem lay = ConvSmem::make(ntx, nty, q2, Q3);
+    float* s_in0 = smem;
+    float* s_w0 = smem + 2 * lay.tile_in;
+    double* s_red = reinterpret_cast<double*>(smem + ((2 * (size_t)lay.tile_in + 2 * (size_t)lay.tile_w + 1) & ~(size_t)1));
+
+    int bt = blockIdx.x;
+    const int t3 = bt % tiles3;
+    bt /= tiles3;
+    const int t2 = bt % tiles2;
+    const int t1 = bt / tiles2;
+    const int64_t S1 = (int64_t)t1 * T1, S2 = (int64_t)t2 * nty, S3 = (int64_t)t3 * ntx * R3;
+    const int bidx = blockIdx.y;
+
+    const float* in = L.in ? L.in + bidx * L.in_bstride : nullptr;
+    float* out = L.out ? L.out + bidx * L.out_bstride : nullptr;
+    const int role = L.role;
+    bool do_conv = true;
+    int cur = 0;
+    double delta = 0.0;
+    if (role == ROLE_FWD_INIT || role == ROLE_FWD_TRIAL || role == ROLE_ADJ_TRIAL) {
+        const IterState* st = L.ctx.st;
+        if (st->done) return;                                   // uniform: the run has finished
+        cur = st->cur;
+        if (role == ROLE_FWD_INIT) {
+            in = L.ctx.x[cur];
+            out = L.ctx.r[cur];
+        } else if (role == ROLE_FWD_TRIAL) {
+            in = L.ctx.x[cur ^ 1];
+            out = L.ctx.r[cur ^ 1];
+        } else {
+            in = L.ctx.r[cur];
+            out = L.ctx.g;
+            delta = st->delta;
+            do_conv = st->need_grad != 0;
+        }
+    }
+
+    float tot[T1][R3];
+#pragma unroll
+    for (int i = 0; i < T1; i++)
+#pragma unroll
+        for (int c = 0; c < R3; c++) tot[i][c] = 0.f;
+
+    const int64_t s2 = S2 + ty;
+    if (do_conv) {
+        const int64_t ulo = max((int64_t)0, S1 + G.o1 - q1 + 1);
+        const int64_t uhi = min(G.a1 - 1, S1 + T1 - 1 + G.o1);
+        const int j2lo = (int)max((int64_t)0, s2 + G.o2 - (G.a2 - 1));
+        const int j2hi = (int)min((int64_t)q2 - 1, s2 + G.o2);
+        const int64_t v0 = S2 + G.o2 - q2 + 1;                  // input row of shared row 0
+        const int64_t c0 = S3 + G.o3 - Q3 + 1;                  // input column of shared column 0
+
+        auto stage = [&](int64_t u, int buf) {
+            float* dst = s_in0 + buf * lay.tile_in;
+            const float* plane = in + u * G.a2 * G.a3;
+            for (int e = tid; e < lay.tile_in; e += nthr) {
+                const int r = e / lay.pitch, c = e - r * lay.pitch;
+                const int64_t v = v0 + r, t = c0 + c;
+                const bool ok = (v >= 0) && (v < G.a2) && (t >= 0) && (t < G.a3);
+                cp_async4(dst + e, ok ? plane + v * G.a3 + t : in, ok);
+            }
+            float* dw = s_w0 + buf * lay.tile_w;
+            const int per = q2 * Q3P;
+            for (int e = tid; e < lay.tile_w; e += nthr) {
+                const int i1 = e / per, rem = e - i1 * per;
+                const int j2 = rem / Q3P, j3 = rem - j2 * Q3P;
+                const int64_t j1 = S1 + i1 + G.o1 - u;
+                const bool ok = (j1 >= 0) && (j1 < q1) && (j3 < Q3);
+                cp_async4(dw + e, ok ? L.w + ((j1 * q2 + j2) * Q3 + j3) : L.w, ok);
+            }
+        };
+
+        if (ulo <= uhi) {
+            stage(ulo, 0);
+            cp_async_commit();
+            for (int64_t u = ulo; u <= uhi; ++u) {
+                const int buf = (int)((u - ulo) & 1);
+                if (u + 1 <= uhi) stage(u + 1, buf ^ 1);
+                cp_async_commit();
+                cp_async_wait1();
+                __syncthreads();
+
+                bool valid[T1];
+#pragma unroll
+                for (int i = 0; i < T1; i++) {
+                    const int64_t j1 = S1 + i + G.o1 - u;
+                    valid[i] = (j1 >= 0) && (j1 < q1) && (S1 + i < G.b1);
+                }
+                float part[T1][R3];
+#pragma unroll
+                for (int i = 0; i < T1; i++)
+#pragma unroll
+                    for (int c = 0; c < R3; c++) part[i][c] = 0.f;
+
+                const float* sin = s_in0 + buf * lay.tile_in + tx * R3;
+                const float* sw = s_w0 + buf * lay.tile_w;
+                for (int j2 = j2lo; j2 <= j2hi; ++j2) {
+                    const float* src = sin + (ty + q2 - 1 - j2) * lay.pitch;
+                    float wv[WLP];
+#pragma unroll
+                    for (int i = 0; i < WLP; i += 4) {
+                        const float4 v = *reinterpret_cast<const float4*>(src + i);
+                        wv[i] = v.x; wv[i + 1] = v.y; wv[i + 2] = v.z; wv[i + 3] = v.w;
+                    }
+#pragma unroll
+                    for (int i = 0; i < T1; i++) {
+                        if (!valid[i]) continue;
+                        const float* hp = sw + (i * q2 + j2) * Q3P;
+#pragma unroll
+                        for (int jj = 0; jj < Q3P; jj += 4) {
+                            const float4 h4 = *reinterpret_cast<const float4*>(hp + jj);
+                            const float hv[4] = {h4.x, h4.y, h4.z, h4.w};
+#pragma unroll
+                            for (int k = 0; k < 4; k++) {
+                                const int j3 = jj + k;
+                                if (j3 < Q3) {
+#pragma unroll
+                                    for (int c = 0; c < R3; c++)
+                                        part[i][c] = fmaf(hv[k], wv[c + Q3 - 1 - j3], part[i][c]);
+                                }
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < T1; i++)
+                    if (valid[i])
+#pragma unroll
+                        for (int c = 0; c < R3; c++) tot[i][c] += part[i][c];
+                __syncthreads();
+            }
+        }
+    }
+
+    // Epilogue.
+    double loc = 0.0;
+    const bool row_ok = s2 < G.b2;
+#pragma unroll
+    for (int i = 0; i < T1; i++) {
+        const int64_t s1 = S1 + i;
+        if (s1 >= G.b1 || !row_ok) continue;
+#pragma unroll
+        for (int c = 0; c < R3; c++) {
+            const int64_t s3 = S3 + (int64_t)tx * R3 + c;
+            if (s3 >= G.b3) continue;
+            const int64_t idx = (s1 * G.b2 + s2) * G.b3 + s3;
+            const float v = tot[i][c];
+            switch (role) {
+            case ROLE_PLAIN:
+                out[idx] = v;
+                break;
+            case ROLE_FWD_INIT:
+            case ROLE_FWD_TRIAL: {
+                const float rr = v - L.ctx.y[idx];
+                out[idx] = rr;
+                loc = fma((double)rr, (double)rr, loc);
+                break;
+            }
+            case ROLE_ADJ_TRIAL: {
+                float gg;
+                if (do_conv) {
+                    gg = v;
+                    out[idx] = gg;
+                } else {
+                    gg = L.ctx.g[idx];
+                }
+                const float xo = L.ctx.x[cur][idx];
+                const double xn_d = fmax((double)xo - delta * (double)gg, 0.0);
+                const float xn = (float)xn_d;
+                L.ctx.x[cur ^ 1][idx] = xn;
+                const double d = (double)xn - (double)xo;
+                loc = fma(d, d, loc);
+                break;
+            }
+            case ROLE_RL_RATIO: {
+                const float yv = L.y[idx];
+                out[idx] = v != 0.f ? yv / v : 0.f;
+                break;
+            }
+            case ROLE_RL_UPDATE: {
+                const float nv = L.ctx.aux[idx];
+                float* x = L.ctx.x[0];
+                x[idx] = nv != 0.f ? x[idx] * (v / nv) : 0.f;
+                break;
+            }
+            default:
+                break;
+            }
+        }
+    }
+    if (role == ROLE_FWD_INIT || role == ROLE_FWD_TRIAL || role == ROLE_ADJ_TRIAL) {
+        const double t = block_sum_f64(loc, s_red);
+        if (tid == 0) {
+            double* part = (role == ROLE_ADJ_TRIAL) ? L.ctx.part_m : L.ctx.part_f;
+            part[blockIdx.y * gridDim.x + blockIdx.x] = t;
+        }
+    }
+}
+
+template <int Q3>
+cudaError_t conv_fp32_launch_q(const ConvLaunch& L, const ConvTile& t, cudaStream_t s)
+{
+    if (L.batch == 0) {       // preparation call (outside any stream capture): opt in to large shared memory
+        return cudaFuncSetAttribute(conv_fp32_kernel<Q3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    }
+    dim3 grid((unsigned)t.grid, (unsigned)L.batch);
+    conv_fp32_kernel<Q3><<<grid, t.ntx * t.nty, t.smem, s>>>(L, t.ntx, t.nty, t.tiles2, t.tiles3);
+    return cudaGetLastError();
+}
+
+#define CDV_INSTANTIATE_FP32(Q) \
+    template cudaError_t conv_fp32_launch_q<Q>(const ConvLaunch&, const ConvTile&, cudaStream_t);
+#define CDV_EXTERN_FP32(Q) \
+    extern template cudaError_t conv_fp32_launch_q<Q>(const ConvLaunch&, const ConvTile&, cudaStream_t);
+
+}  // namespace cdv

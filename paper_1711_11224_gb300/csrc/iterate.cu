@@ -1,0 +1,196 @@
+// Device-side control of the projected-gradient iteration (Steps 1-3 of the
+// 2-D application, any n) and its elementwise helpers.
+//
+// One step of the run is a fixed three-launch "trial slot":
+//   1. adjoint trial  g = A^T r_k (skipped after a rejected trial, g reused),
+//                     x_t = max(x_k - delta g, 0), partials of ||x_t - x_k||^2
+//   2. forward trial  r_t = A x_t - y, partials of ||r_t||^2
+//   3. decide         f_t = 1/2 ||r_t||^2 (FP64, fixed-order reduction);
+//                     accept if f_t < f_k (the decrease rule of Step 2),
+//                     else delta <- beta * delta and retry from x_k.
+// All decisions live in IterState on the device, so the slots of a whole run
+// can be captured in one CUDA graph and replayed without host round trips.
+// Slots after the run has finished return at once.
+#include <math.h>
+
+#include <algorithm>
+
+#include "cdv_internal.h"
+
+namespace cdv {
+
+__global__ void x0_kernel(int policy, float* x, const float* y, int64_t m1, int64_t m2, int64_t m3, int p1,
+                          int p2, int p3)
+{
+    const int64_t n = m1 * m2 * m3;
+    const int64_t n2 = m2 + 2 * p2, n3 = m3 + 2 * p3;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (policy == CDV_X0_ZERO) {
+            x[i] = 0.f;
+        } else {
+            const int64_t k3 = i % m3, k2 = (i / m3) % m2, k1 = i / (m2 * m3);
+            const float v = y[((k1 + p1) * n2 + (k2 + p2)) * n3 + (k3 + p3)];
+            x[i] = v > 0.f ? v : 0.f;
+        }
+    }
+}
+
+cudaError_t launch_x0(int policy, float* x, const float* y, int64_t m1, int64_t m2, int64_t m3, int p1, int p2,
+                      int p3, cudaStream_t s)
+{
+    if (policy == CDV_X0_GIVEN) return cudaSuccess;
+    const int64_t n = m1 * m2 * m3;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+    x0_kernel<<<blocks, 256, 0, s>>>(policy, x, y, m1, m2, m3, p1, p2, p3);
+    return cudaGetLastError();
+}
+
+__global__ void state_init_kernel(IterState* st, double delta0, const double* absum, double beta, int max_halvings,
+                                  int max_rejects, int K, int hist_cap)
+{
+    if (!(delta0 > 0.0)) {                // default step 1/L, L = (sum |h|)^2 >= ||A||_2^2
+        const double a = *absum;
+        delta0 = 1.0 / (a * a);
+    }
+    st->f_cur = 0.0;
+    st->f_trial = 0.0;
+    st->delta = delta0;
+    st->delta0 = delta0;
+    st->beta = beta;
+    st->moved = 0.0;
+    st->accepted = 0;
+    st->rejected = 0;
+    st->halvings = 0;
+    st->max_halvings = max_halvings;
+    st->max_rejects = max_rejects;
+    st->K = K;
+    st->cur = 0;
+    st->need_grad = 1;
+    st->done = 0;
+    st->status = CDV_OK;
+    st->trials = 0;
+    st->hist_cap = hist_cap;
+    st->adj_convs = 0;
+    st->pad_ = 0;
+}
+
+cudaError_t launch_state_init(IterState* st, double delta0, const double* absum, double beta, int max_halvings,
+                              int max_rejects, int K, int hist_cap, cudaStream_t s)
+{
+    state_init_kernel<<<1, 1, 0, s>>>(st, delta0, absum, beta, max_halvings, max_rejects, K, hist_cap);
+    return cudaGetLastError();
+}
+
+// Deterministic FP64 sum of n partials by one block: strided per-thread sums
+// in index order, then a fixed shared-memory tree.
+__device__ double block_reduce_fixed(const double* a, int n, double* sh)
+{
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += a[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    const double t = sh[0];
+    __syncthreads();
+    return t;
+}
+
+__global__ void __launch_bounds__(512) decide_kernel(IterCtx c, int nf, int nm, int init)
+{
+    __shared__ double sh[512];
+    IterState* st = c.st;
+    if (st->done) return;
+    const double F = 0.5 * block_reduce_fixed(c.part_f, nf, sh);
+    const double M = init ? 0.0 : block_reduce_fixed(c.part_m, nm, sh);
+    if (threadIdx.x != 0) return;
+    if (init) {
+        st->f_cur = F;
+        c.f_hist[0] = F;
+        st->need_grad = 1;
+        if (!isfinite(F)) {
+            st->status = CDV_ERR_NONFINITE;
+            st->done = 1;
+        } else if (st->K <= 0) {
+            st->done = 1;
+        }
+        return;
+    }
+    st->trials += 1;
+    if (st->need_grad) st->adj_convs += 1;
+    st->f_trial = F;
+    st->moved = M;
+    if (M == 0.0) {                       // x_t == x_k: stationary point, the run has converged
+        st->status = CDV_ERR_NOT_DESCENDING;
+        st->done = 1;
+        return;
+    }
+    if (!isfinite(F)) {
+        st->status = CDV_ERR_NONFINITE;
+        st->done = 1;
+        return;
+    }
+    if (F < st->f_cur) {                  // f(x_{k+1}) < f(x_k): accept
+        const int a = st->accepted;
+        if (a < st->hist_cap) {
+            c.d_hist[a] = st->delta;
+            c.f_hist[a + 1] = F;
+        }
+        st->accepted = a + 1;
+        st->cur ^= 1;
+        st->f_cur = F;
+        st->halvings = 0;
+        st->delta = st->delta0;
+        st->need_grad = 1;
+        if (st->accepted >= st->K) st->done = 1;
+    } else {                              // reject: shorten the step, keep x_k and g_k
+        st->rejected += 1;
+        st->halvings += 1;
+        st->need_grad = 0;
+        if (st->halvings > st->max_halvings || st->rejected > st->max_rejects) {
+            st->status = CDV_ERR_NOT_DESCENDING;
+            st->done = 1;
+        } else {
+            st->delta *= st->beta;
+        }
+    }
+}
+
+cudaError_t launch_decide(const IterCtx& c, int nparts_f, int nparts_m, int init, cudaStream_t s)
+{
+    decide_kernel<<<1, 512, 0, s>>>(c, nparts_f, nparts_m, init);
+    return cudaGetLastError();
+}
+
+__global__ void finalize_kernel(IterCtx c, int64_t nx)
+{
+    if (c.st->cur == 0) return;
+    const float* src = c.x[1];
+    float* dst = c.x[0];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nx; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+cudaError_t launch_finalize(const IterCtx& c, int64_t nx, cudaStream_t s)
+{
+    const int blocks = (int)std::min<int64_t>((nx + 255) / 256, 152 * 8);
+    finalize_kernel<<<blocks, 256, 0, s>>>(c, nx);
+    return cudaGetLastError();
+}
+
+__global__ void fill_kernel(float* x, int64_t n, float v)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = v;
+}
+
+cudaError_t launch_fill(float* x, int64_t n, float v, cudaStream_t s)
+{
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+    fill_kernel<<<blocks, 256, 0, s>>>(x, n, v);
+    return cudaGetLastError();
+}
+
+}  // namespace cdv

@@ -1,0 +1,140 @@
+"""GPU parity of the projected-gradient iteration (Steps 1-3) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from _util import TOL_ITER, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _run(P, K, **kw):
+    from paper_1711_11224_gb300 import Plan
+    with Plan(P.m, P.p) as pl:
+        pl.set_psf(_dev(P.H))
+        X0 = oracle.x0_crop(P.Y, P.p).astype(np.float32)
+        X, rep = pl.iterate(_dev(P.Y), _dev(X0), K=K, **kw)
+        return X.cpu().numpy(), rep
+
+
+def _check(P, K, tol=TOL_ITER, **kw):
+    Xg, rep = _run(P, K, **kw)
+    ref = oracle.iterate(P.Y, P.H, oracle.x0_crop(P.Y, P.p), K,
+                         delta0=kw.get("delta0"), beta=kw.get("beta", 0.5))
+    assert rep["accepted"] == ref["accepted"] == K
+    assert rep["status"] == "CDV_OK"
+    assert rel_l2(Xg, ref["X"]) <= tol
+    np.testing.assert_allclose(rep["f"], ref["f"], rtol=1e-5)
+    assert np.all(np.diff(rep["f"]) < 0)                  # the decrease rule of Step 2
+    assert np.all(Xg >= 0)
+    return Xg, rep, ref
+
+
+def test_blobs2d_full():
+    """64x64, 7x7 Gaussian, 50 iterations (n = 2)."""
+    P = synth.blobs2d()
+    _check(P, P.K)
+
+
+def test_fil3d_small_several_tiles():
+    """15x15x11 template on a 40x48x36 filament volume: several tiles and ragged tails, 20 iterations."""
+    P = synth.scaled_fil3d((40, 48, 36), (15, 15, 11), K=20)
+    _check(P, 20)
+
+
+def test_fil3d_full_100_iterations():
+    """256x256x64, 15x15x11 Gaussian, Poisson data, 100 iterations: rel-L2 <= 1e-4 vs FP64."""
+    P = synth.fil3d()
+    Xg, rep, ref = _check(P, 100)
+    assert rep["gmac"] > 0
+
+
+def test_graph_and_stream_paths_agree_and_repeat():
+    P = synth.scaled_fil3d((20, 33, 41), (5, 7, 9), K=10)
+    a, ra = _run(P, 10, use_graph=True)
+    b, rb = _run(P, 10, use_graph=False)
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(ra["f"], rb["f"])
+    from paper_1711_11224_gb300 import Plan
+    with Plan(P.m, P.p) as pl:                            # replay of the cached graph is deterministic
+        pl.set_psf(_dev(P.H))
+        X0 = oracle.x0_crop(P.Y, P.p).astype(np.float32)
+        Y = _dev(P.Y)
+        X = _dev(X0)
+        outs = []
+        for _ in range(3):
+            X.copy_(_dev(X0))
+            pl.iterate(Y, X, K=10)
+            outs.append(X.cpu().numpy())
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(outs[0], outs[2])
+    np.testing.assert_array_equal(outs[0], a)
+
+
+def test_x0_policies():
+    from paper_1711_11224_gb300 import Plan
+    P = synth.scaled_fil3d((12, 20, 28), (3, 5, 7), K=5)
+    with Plan(P.m, P.p) as pl:
+        pl.set_psf(_dev(P.H))
+        X, rep = pl.iterate(_dev(P.Y), K=0, x0="crop")
+        np.testing.assert_array_equal(X.cpu().numpy(), oracle.x0_crop(P.Y, P.p).astype(np.float32))
+        assert rep["accepted"] == 0
+        np.testing.assert_allclose(rep["f0"], oracle.objective(oracle.x0_crop(P.Y, P.p), P.H, P.Y), rtol=1e-6)
+        X, rep = pl.iterate(_dev(P.Y), _dev(np.ones(P.m)), K=3, x0="zero")
+        ref = oracle.iterate(P.Y, P.H, np.zeros(P.m), 3)
+        assert rel_l2(X.cpu().numpy(), ref["X"]) <= TOL_ITER
+
+
+def test_backtracking_matches_oracle():
+    """delta0 = 8/L forces rejections: the accepted/rejected counts and deltas follow the FP64 rule."""
+    P = synth.blobs2d()
+    d0 = 8.0 / oracle.lipschitz(P.H)
+    Xg, rep = _run(P, 10, delta0=d0)
+    ref = oracle.iterate(P.Y, P.H, oracle.x0_crop(P.Y, P.p), 10, delta0=d0)
+    assert rep["accepted"] == ref["accepted"] == 10
+    assert rep["rejected"] == ref["rejected"] > 0
+    np.testing.assert_allclose(rep["delta"], ref["delta"], rtol=1e-12)
+    assert rel_l2(Xg, ref["X"]) <= TOL_ITER
+
+
+def test_identity_template_converges():
+    """H = delta (A = I): one accepted step reaches max(Y, 0), then the run stops as converged."""
+    from paper_1711_11224_gb300 import Plan
+    rng = np.random.default_rng(1)
+    Y = rng.standard_normal((6, 7, 9)).astype(np.float32)
+    with Plan((6, 7, 9), (0, 0, 0)) as pl:
+        pl.set_psf(_dev(np.ones((1, 1, 1))))
+        X, rep = pl.iterate(_dev(Y), _dev(np.full((6, 7, 9), 0.5)), K=5)
+    np.testing.assert_array_equal(X.cpu().numpy(), np.maximum(Y, 0))
+    assert rep["accepted"] == 1 and rep["status"] == "CDV_ERR_NOT_DESCENDING"
+
+
+def test_iterate_host_matches_device():
+    from paper_1711_11224_gb300 import Plan
+    P = synth.scaled_fil3d((16, 30, 40), (5, 5, 7), K=8)
+    X0 = oracle.x0_crop(P.Y, P.p).astype(np.float32)
+    a, _ = _run(P, 8)
+    with Plan(P.m, P.p) as pl:
+        pl.set_psf(_dev(P.H))
+        Xh = X0.copy()
+        pl.iterate_host(P.Y, Xh, K=8)
+    np.testing.assert_array_equal(Xh, a)
+
+
+def test_richardson_lucy_matches_oracle():
+    from paper_1711_11224_gb300 import Plan
+    P = synth.scaled_fil3d((14, 26, 30), (5, 7, 5), K=10)
+    X0 = np.full(P.m, float(P.Y.mean()), np.float32)
+    with Plan(P.m, P.p) as pl:
+        pl.set_psf(_dev(P.H))
+        X = _dev(X0)
+        pl.richardson_lucy(_dev(P.Y), X, 10)
+        Xg = X.cpu().numpy()
+    ref = oracle.richardson_lucy(P.Y, P.H, X0, 10)
+    assert rel_l2(Xg, ref) <= TOL_ITER
