@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample-planes", type=int, default=96)
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="time the forward and adjoint kernels alone (launch order: forward, adjoint, forward, adjoint)")
     return ap.parse_args()
 
 
@@ -186,6 +188,35 @@ def time_kernel(fn, stream, reps=3):
     b.record(stream)
     b.synchronize()
     return a.elapsed_time(b) / reps / 1e3
+
+
+def run_kernels_only(args):
+    import torch
+    from paper_1711_11224_gb300 import Plan
+    P = problem(args.workload)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    pl = Plan(P.m, P.p, mode=args.mode)
+    pl.set_psf(torch.from_numpy(P.H).to(dev))
+    X = torch.from_numpy(P.X_true).to(dev)
+    R = torch.empty(P.Y.shape, device=dev, dtype=torch.float32)
+    G = torch.empty(P.m, device=dev, dtype=torch.float32)
+    pl.forward(X, R)                              # warm-up launches: forward, adjoint
+    pl.adjoint(R, G)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record(stream)
+    pl.forward(X, R)                              # timed launches: forward, adjoint
+    ev[1].record(stream)
+    pl.adjoint(R, G)
+    ev[2].record(stream)
+    ev[2].synchronize()
+    tf = ev[0].elapsed_time(ev[1]) / 1e3
+    ta = ev[1].elapsed_time(ev[2]) / 1e3
+    flops = 2.0 * float(np.prod(P.m)) * float(P.H.size)
+    print(json.dumps({"workload": args.workload, "forward_ms": tf * 1e3, "adjoint_ms": ta * 1e3,
+                      "forward_tflops": flops / tf / 1e12, "adjoint_tflops": flops / ta / 1e12}), flush=True)
+    pl.close()
 
 
 def run_cdv(args):
@@ -329,6 +360,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.kernels_only:
+        run_kernels_only(args)
     else:
         run_cdv(args)
 
