@@ -125,6 +125,25 @@ cdv_status cdv_adjoint(cdv_plan* plan, int batch, const float* R, float* G, void
 cdv_status cdv_grad_psf(cdv_plan* plan, int batch, const float* X, const float* dY, float* dH,
                         void* stream);
 
+/*
+ * cdv_grad_psf for callers that cannot allocate device memory (for example
+ * code running during a global-mode CUDA graph capture, or a plug-in whose
+ * host framework owns all device memory).  The paper has no counterpart:
+ * this is a deployment variant of the template gradient above.
+ *
+ * No plan: n, m[0..n-1] and p[0..n-1] describe the problem as in
+ * cdv_plan_create; X, dY and dH are as in cdv_grad_psf and owned by the
+ * caller.  The call allocates nothing.  Its FP64 partials live in a
+ * library-wide static device array of 4 MiB (held by every GPU that loads
+ * the library, until exit), so the template may have at most 524288 samples
+ * (larger: CDV_ERR_UNSUPPORTED, nothing enqueued).  The first call on each
+ * device looks up the array's address and must come before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race,
+ * so order them on one stream.  Asynchronous on `stream`.
+ */
+cdv_status cdv_grad_psf_static(int n, const int64_t* m, const int32_t* p, int batch, const float* X,
+                               const float* dY, float* dH, void* stream);
+
 /* Initial solution of Step 1 (the paper leaves it open). */
 typedef enum {
     CDV_X0_GIVEN = 0,   /* X holds x_0 on entry */

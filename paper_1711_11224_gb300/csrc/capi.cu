@@ -43,6 +43,8 @@ constexpr int kHistCap = 65536;
 
 }  // namespace
 
+void cdv::set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
 struct cdv_plan {
     int device = 0;
     int n = 0;

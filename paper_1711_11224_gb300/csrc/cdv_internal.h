@@ -109,6 +109,9 @@ size_t grad_psf_partials(const GradPsfPlan& g);
 cudaError_t launch_grad_psf(const GradPsfPlan& g, const float* X, const float* dY, double* partial,
                             float* dH, cudaStream_t s);
 
+// Message returned by cdv_last_error() on this host thread (capi.cu).
+void set_last_error(const char* msg);
+
 // Elementwise helpers (iterate.cu).
 cudaError_t launch_fill(float* x, int64_t n, float v, cudaStream_t s);
 
