@@ -20,8 +20,8 @@ ConvTile conv_fp32_tile(const ConvGeom& g)
     t.ntx = (int)((cols + t.tiles3 - 1) / t.tiles3);
     int nty = std::max(1, kMaxThreads / t.ntx);
     nty = (int)std::min<int64_t>(nty, g.b2);
-    // keep the staged tiles within the shared-memory budget
-    while (nty > 1 && ConvSmem::make(t.ntx, nty, g.q2, g.q3).bytes() > 200 * 1024) nty--;
+    // two CTAs per SM: at most 110 KB of shared memory each
+    while (nty > 1 && ConvSmem::make(t.ntx, nty, g.q2, g.q3).bytes() > 110 * 1024) nty--;
     t.nty = nty;
     t.tiles2 = (int)((g.b2 + nty - 1) / nty);
     t.tiles1 = (int)((g.b1 + kT1 - 1) / kT1);

@@ -36,7 +36,7 @@ namespace cdv {
 
 constexpr int kR3 = 8;        // outputs per thread along the contiguous axis
 constexpr int kT1 = 4;        // output planes per CTA (and per thread)
-constexpr int kMaxThreads = 320;
+constexpr int kMaxThreads = 256;
 
 __host__ __device__ constexpr int ceil4(int v) { return (v + 3) & ~3; }
 
@@ -64,28 +64,38 @@ __device__ __forceinline__ double block_sum_f64(double v, double* s_red)
     return t;
 }
 
-// Shared-memory layout of one CTA (in floats).
+// Shared-memory layout of one CTA (in floats):
+//   [input tile, 2 buffers][template ring, T1+1 planes][running totals][FP64 scratch]
+// The template ring holds plane j1 in slot j1 mod (T1+1): consecutive input
+// planes u need the template planes j1 = s1 + o1 - u of the CTA's T1 output
+// planes, a window that slides by one plane per u, so one new plane is staged
+// per input plane.  Running totals are stored [T1*R3][threads] (thread index
+// fastest: conflict-free).
 struct ConvSmem {
-    int rows, pitch, tile_in, tile_w;
+    int rows, pitch, tile_in, wplane, tile_w, tot;
     __host__ __device__ static ConvSmem make(int ntx, int nty, int q2, int q3)
     {
         ConvSmem s;
         s.rows = nty + q2 - 1;
         s.pitch = ceil4((ntx - 1) * kR3 + ceil4(kR3 + q3 - 1));
         s.tile_in = s.rows * s.pitch;
-        s.tile_w = kT1 * q2 * ceil4(q3);
+        s.wplane = q2 * ceil4(q3);
+        s.tile_w = (kT1 + 1) * s.wplane;
+        s.tot = kT1 * kR3 * ntx * nty;
         return s;
     }
-    __host__ __device__ size_t bytes() const
+    __host__ __device__ size_t floats() const
     {
-        size_t f = 2 * (size_t)tile_in + 2 * (size_t)tile_w;
-        f = (f + 1) & ~(size_t)1;                       // 8-byte align the FP64 scratch
-        return f * sizeof(float) + 32 * sizeof(double);
+        size_t f = 2 * (size_t)tile_in + (size_t)tile_w + (size_t)tot;
+        return (f + 1) & ~(size_t)1;                    // 8-byte align the FP64 scratch
     }
+    __host__ __device__ size_t bytes() const { return floats() * sizeof(float) + 32 * sizeof(double); }
 };
 
+__device__ __forceinline__ int ring_slot(int64_t j1) { return (int)(((j1 % (kT1 + 1)) + (kT1 + 1)) % (kT1 + 1)); }
+
 template <int Q3>
-__global__ void __launch_bounds__(kMaxThreads, 1)
+__global__ void __launch_bounds__(kMaxThreads, 2)
 conv_fp32_kernel(const ConvLaunch L, const int ntx, const int nty, const int tiles2, const int tiles3)
 {
     constexpr int R3 = kR3, T1 = kT1;
@@ -94,14 +104,19 @@ conv_fp32_kernel(const ConvLaunch L, const int ntx, const int nty, const int til
     extern __shared__ __align__(16) float smem[];
 
     const ConvGeom& G = L.g;
+    // The block has whole warps (blockDim.x = nthr rounded up to 32); threads
+    // past nthr only help stage shared memory.
     const int tid = threadIdx.x;
-    const int tx = tid % ntx, ty = tid / ntx;
     const int nthr = ntx * nty;
+    const bool active = tid < nthr;
+    const int tx = active ? tid % ntx : 0, ty = active ? tid / ntx : 0;
+    const int lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
     const int q1 = G.q1, q2 = G.q2;
     const ConvSmem lay = ConvSmem::make(ntx, nty, q2, Q3);
     float* s_in0 = smem;
-    float* s_w0 = smem + 2 * lay.tile_in;
-    double* s_red = reinterpret_cast<double*>(smem + ((2 * (size_t)lay.tile_in + 2 * (size_t)lay.tile_w + 1) & ~(size_t)1));
+    float* s_w = smem + 2 * lay.tile_in;
+    float* s_tot = s_w + lay.tile_w;
+    double* s_red = reinterpret_cast<double*>(smem + lay.floats());
 
     int bt = blockIdx.x;
     const int t3 = bt % tiles3;
@@ -135,56 +150,64 @@ conv_fp32_kernel(const ConvLaunch L, const int ntx, const int nty, const int til
         }
     }
 
-    float tot[T1][R3];
+    if (active)
 #pragma unroll
-    for (int i = 0; i < T1; i++)
-#pragma unroll
-        for (int c = 0; c < R3; c++) tot[i][c] = 0.f;
+        for (int k = 0; k < T1 * R3; k++) s_tot[k * nthr + tid] = 0.f;
 
     const int64_t s2 = S2 + ty;
     if (do_conv) {
         const int64_t ulo = max((int64_t)0, S1 + G.o1 - q1 + 1);
         const int64_t uhi = min(G.a1 - 1, S1 + T1 - 1 + G.o1);
         const int j2lo = (int)max((int64_t)0, s2 + G.o2 - (G.a2 - 1));
-        const int j2hi = (int)min((int64_t)q2 - 1, s2 + G.o2);
+        const int j2hi = active ? (int)min((int64_t)q2 - 1, s2 + G.o2) : -1;
         const int64_t v0 = S2 + G.o2 - q2 + 1;                  // input row of shared row 0
         const int64_t c0 = S3 + G.o3 - Q3 + 1;                  // input column of shared column 0
 
-        auto stage = [&](int64_t u, int buf) {
+        // one warp per shared row, lanes along the row: no index division
+        auto stage_in = [&](int64_t u, int buf) {
             float* dst = s_in0 + buf * lay.tile_in;
             const float* plane = in + u * G.a2 * G.a3;
-            for (int e = tid; e < lay.tile_in; e += nthr) {
-                const int r = e / lay.pitch, c = e - r * lay.pitch;
-                const int64_t v = v0 + r, t = c0 + c;
-                const bool ok = (v >= 0) && (v < G.a2) && (t >= 0) && (t < G.a3);
-                cp_async4(dst + e, ok ? plane + v * G.a3 + t : in, ok);
+            for (int r = wid; r < lay.rows; r += nwarps) {
+                const int64_t v = v0 + r;
+                const bool rok = (v >= 0) && (v < G.a2);
+                const float* src = plane + v * G.a3;
+                for (int c = lane; c < lay.pitch; c += 32) {
+                    const int64_t t = c0 + c;
+                    const bool ok = rok && (t >= 0) && (t < G.a3);
+                    cp_async4(dst + r * lay.pitch + c, ok ? src + t : in, ok);
+                }
             }
-            float* dw = s_w0 + buf * lay.tile_w;
-            const int per = q2 * Q3P;
-            for (int e = tid; e < lay.tile_w; e += nthr) {
-                const int i1 = e / per, rem = e - i1 * per;
-                const int j2 = rem / Q3P, j3 = rem - j2 * Q3P;
-                const int64_t j1 = S1 + i1 + G.o1 - u;
-                const bool ok = (j1 >= 0) && (j1 < q1) && (j3 < Q3);
-                cp_async4(dw + e, ok ? L.w + ((j1 * q2 + j2) * Q3 + j3) : L.w, ok);
-            }
+        };
+        auto stage_w = [&](int64_t j1) {                        // template plane j1 into its ring slot
+            if (j1 < 0 || j1 >= q1) return;
+            float* dst = s_w + ring_slot(j1) * lay.wplane;
+            const float* src = L.w + j1 * q2 * Q3;
+            for (int r = wid; r < q2; r += nwarps)
+                for (int c = lane; c < Q3P; c += 32)
+                    cp_async4(dst + r * Q3P + c, c < Q3 ? src + r * Q3 + c : L.w, c < Q3);
         };
 
         if (ulo <= uhi) {
-            stage(ulo, 0);
+            stage_in(ulo, 0);
+            for (int i = 0; i < T1; i++) stage_w(S1 + i + G.o1 - ulo);
             cp_async_commit();
             for (int64_t u = ulo; u <= uhi; ++u) {
                 const int buf = (int)((u - ulo) & 1);
-                if (u + 1 <= uhi) stage(u + 1, buf ^ 1);
+                if (u + 1 <= uhi) {
+                    stage_in(u + 1, buf ^ 1);
+                    stage_w(S1 + G.o1 - (u + 1));               // the one plane that enters the window
+                }
                 cp_async_commit();
                 cp_async_wait1();
                 __syncthreads();
 
                 bool valid[T1];
+                int woff[T1];
 #pragma unroll
                 for (int i = 0; i < T1; i++) {
                     const int64_t j1 = S1 + i + G.o1 - u;
                     valid[i] = (j1 >= 0) && (j1 < q1) && (S1 + i < G.b1);
+                    woff[i] = ring_slot(j1) * lay.wplane;
                 }
                 float part[T1][R3];
 #pragma unroll
@@ -193,7 +216,6 @@ conv_fp32_kernel(const ConvLaunch L, const int ntx, const int nty, const int til
                     for (int c = 0; c < R3; c++) part[i][c] = 0.f;
 
                 const float* sin = s_in0 + buf * lay.tile_in + tx * R3;
-                const float* sw = s_w0 + buf * lay.tile_w;
                 for (int j2 = j2lo; j2 <= j2hi; ++j2) {
                     const float* src = sin + (ty + q2 - 1 - j2) * lay.pitch;
                     float wv[WLP];
@@ -205,7 +227,7 @@ conv_fp32_kernel(const ConvLaunch L, const int ntx, const int nty, const int til
 #pragma unroll
                     for (int i = 0; i < T1; i++) {
                         if (!valid[i]) continue;
-                        const float* hp = sw + (i * q2 + j2) * Q3P;
+                        const float* hp = s_w + woff[i] + j2 * Q3P;
 #pragma unroll
                         for (int jj = 0; jj < Q3P; jj += 4) {
                             const float4 h4 = *reinterpret_cast<const float4*>(hp + jj);
@@ -222,11 +244,12 @@ conv_fp32_kernel(const ConvLaunch L, const int ntx, const int nty, const int til
                         }
                     }
                 }
+                if (active)
 #pragma unroll
-                for (int i = 0; i < T1; i++)
-                    if (valid[i])
+                    for (int i = 0; i < T1; i++)
+                        if (valid[i])
 #pragma unroll
-                        for (int c = 0; c < R3; c++) tot[i][c] += part[i][c];
+                            for (int c = 0; c < R3; c++) s_tot[(i * R3 + c) * nthr + tid] += part[i][c];
                 __syncthreads();
             }
         }
@@ -234,7 +257,7 @@ conv_fp32_kernel(const ConvLaunch L, const int ntx, const int nty, const int til
 
     // Epilogue.
     double loc = 0.0;
-    const bool row_ok = s2 < G.b2;
+    const bool row_ok = active && s2 < G.b2;
 #pragma unroll
     for (int i = 0; i < T1; i++) {
         const int64_t s1 = S1 + i;
@@ -244,7 +267,7 @@ conv_fp32_kernel(const ConvLaunch L, const int ntx, const int nty, const int til
             const int64_t s3 = S3 + (int64_t)tx * R3 + c;
             if (s3 >= G.b3) continue;
             const int64_t idx = (s1 * G.b2 + s2) * G.b3 + s3;
-            const float v = tot[i][c];
+            const float v = s_tot[(i * R3 + c) * nthr + tid];
             switch (role) {
             case ROLE_PLAIN:
                 out[idx] = v;
@@ -304,7 +327,8 @@ cudaError_t conv_fp32_launch_q(const ConvLaunch& L, const ConvTile& t, cudaStrea
         return cudaFuncSetAttribute(conv_fp32_kernel<Q3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     }
     dim3 grid((unsigned)t.grid, (unsigned)L.batch);
-    conv_fp32_kernel<Q3><<<grid, t.ntx * t.nty, t.smem, s>>>(L, t.ntx, t.nty, t.tiles2, t.tiles3);
+    const int threads = (t.ntx * t.nty + 31) & ~31;
+    conv_fp32_kernel<Q3><<<grid, threads, t.smem, s>>>(L, t.ntx, t.nty, t.tiles2, t.tiles3);
     return cudaGetLastError();
 }
 
