@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--impl", default="cdv", choices=["cdv", "reference"])
     ap.add_argument("--workload", default="ring3d", choices=sorted(WORKLOADS))
     ap.add_argument("--mode", default="fp32", choices=["fp32", "bf16", "tf32", "split3"])
+    ap.add_argument("--path", default="auto", choices=["auto", "general", "small"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample-planes", type=int, default=96)
@@ -242,7 +243,7 @@ def run_cdv(args):
     # warm-up: at least W steps, and the K-step graph captured outside the clock
     done = 0
     while True:
-        _, rep = pl.iterate(Y, X, K=K, x0="crop")
+        _, rep = pl.iterate(Y, X, K=K, x0="crop", path=args.path)
         done += K
         if done >= args.warmup:
             break
@@ -254,7 +255,7 @@ def run_cdv(args):
     ev1 = torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
         ev0.record(stream)
-        _, rep = pl.iterate(Y, X, K=K, x0="crop")
+        _, rep = pl.iterate(Y, X, K=K, x0="crop", path=args.path)
         ev1.record(stream)
         torch.cuda.synchronize()
     if dist:
@@ -273,6 +274,7 @@ def run_cdv(args):
            "ms_per_step": t * 1e3 / max(1, rep["accepted"]), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32" if args.mode == "fp32" else args.mode, "data": "synthetic",
            "config": {"workload": "%s: %s" % (args.workload, WORKLOADS[args.workload]), "mode": args.mode,
+                      "path": args.path,
                       "K_per_call": K, "accepted": rep["accepted"], "rejected": rep["rejected"],
                       "status": rep["status"], "parallelism": "independent problem per GPU" if ws > 1 else "1 GPU",
                       "l2": "inputs larger than L2 (Y %.0f MB, X %.0f MB > 129 MB)"
@@ -303,12 +305,12 @@ def run_cdv(args):
         Yh.copy_(torch.from_numpy(P.Y))
         Xh = torch.empty(P.m, dtype=torch.float32, pin_memory=True)
         Yn, Xn = Yh.numpy(), Xh.numpy()
-        pl.iterate_host(Yn, Xn, K=K, x0="crop", report=False)    # capture its graph outside the clock
+        pl.iterate_host(Yn, Xn, K=K, x0="crop", report=False, path=args.path)   # graph captured outside the clock
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
-        _, rep2 = pl.iterate_host(Yn, Xn, K=K, x0="crop")
+        _, rep2 = pl.iterate_host(Yn, Xn, K=K, x0="crop", path=args.path)
         te = time.perf_counter() - t0
         if dist:
             tt = torch.tensor([te], device=dev, dtype=torch.float64)

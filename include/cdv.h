@@ -158,8 +158,18 @@ typedef struct {
     int max_halvings;   /* rejected trials allowed within one step, default 20 */
     int max_rejects;    /* rejected trials allowed in the whole run, default 16 */
     int use_graph;      /* 1: replay the captured K-step sequence as a CUDA graph (default) */
-    int reserved[4];
+    int path;           /* cdv_iter_path, default CDV_PATH_AUTO */
+    int reserved[3];
 } cdv_iter_opts;
+
+/* Which kernels run the iteration. */
+typedef enum {
+    CDV_PATH_AUTO = 0,      /* the single-CTA path when the problem fits in one SM, else the general one */
+    CDV_PATH_GENERAL = 1,   /* per-step forward/adjoint launches over the whole GPU (CUDA graph) */
+    CDV_PATH_SMALL = 2      /* one CTA holds the whole problem in shared memory and runs all K steps
+                               in one launch; CDV_ERR_UNSUPPORTED if it does not fit (template width
+                               along the contiguous axis <= 15, about 200 KB of state) */
+} cdv_iter_path;
 
 /* Fill `o` with the defaults above. */
 void cdv_iter_opts_default(cdv_iter_opts* o);

@@ -21,6 +21,7 @@ STATUS = {
 }
 MODES = {"fp32": 0, "bf16": 1, "tf32": 2, "split3": 3}
 X0 = {"given": 0, "crop": 1, "zero": 2}
+PATHS = {"auto": 0, "general": 1, "small": 2}
 
 # Every symbol include/cdv.h declares (checked by the tests).
 EXPORTS = [
@@ -40,7 +41,7 @@ class CdvError(RuntimeError):
 class IterOpts(ctypes.Structure):
     _fields_ = [("x0_policy", ctypes.c_int), ("delta0", ctypes.c_double), ("beta", ctypes.c_double),
                 ("max_halvings", ctypes.c_int), ("max_rejects", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("path", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class IterReport(ctypes.Structure):

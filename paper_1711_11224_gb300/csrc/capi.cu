@@ -201,6 +201,14 @@ cdv_status cdv_plan_create(cdv_plan** out, int n, const int64_t* m, const int32_
     cudaError_t e = cudaGetDevice(&P->device);
     if (e == cudaSuccess) e = conv_fp32_prepare(P->q[2]);
     if (e == cudaSuccess) e = grad_psf_prepare();
+    if (e == cudaSuccess && small_supported(P->m, P->p)) {
+        SmallRun r{};
+        for (int i = 0; i < 3; i++) {
+            r.m[i] = P->m[i];
+            r.p[i] = P->p[i];
+        }
+        e = small_iterate(r, nullptr, true);
+    }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = P->alloc(&P->H, P->nh);
     if (e == cudaSuccess) e = P->alloc(&P->Ht, P->nh);
@@ -386,8 +394,37 @@ cdv_status cdv_iterate(cdv_plan* plan, const float* Y, float* X, int K, const cd
     if (!(o.beta > 0.0 && o.beta < 1.0)) return fail(CDV_ERR_INVALID_ARG, "beta = %g", o.beta);
     if (o.max_halvings < 0 || o.max_rejects < 0 || o.max_rejects > 1 << 20)
         return fail(CDV_ERR_INVALID_ARG, "max_halvings/max_rejects");
+    if (o.path < CDV_PATH_AUTO || o.path > CDV_PATH_SMALL) return fail(CDV_ERR_INVALID_ARG, "path = %d", o.path);
     const double delta0 = o.delta0 > 0.0 ? o.delta0 : 0.0;
     cudaStream_t s = (cudaStream_t)stream;
+    const bool small_ok = small_supported(plan->m, plan->p);
+    if (o.path == CDV_PATH_SMALL && !small_ok)
+        return fail(CDV_ERR_UNSUPPORTED, "problem does not fit the single-CTA path (%zu bytes of shared memory)",
+                    small_smem_bytes(plan->m, plan->p));
+    if (o.path == CDV_PATH_SMALL || (o.path == CDV_PATH_AUTO && small_ok)) {
+        SmallRun r{};
+        for (int i = 0; i < 3; i++) {
+            r.m[i] = plan->m[i];
+            r.p[i] = plan->p[i];
+        }
+        r.y = Y;
+        r.x = X;
+        r.h = plan->H;
+        r.st = plan->st;
+        r.f_hist = plan->f_hist;
+        r.d_hist = plan->d_hist;
+        r.hist_cap = kHistCap;
+        r.K = K;
+        r.x0_policy = o.x0_policy;
+        r.max_halvings = o.max_halvings;
+        r.max_rejects = o.max_rejects;
+        r.delta0 = delta0;
+        r.beta = o.beta;
+        r.absum = plan->absum;
+        CDV_CUDA(small_iterate(r, s, false), "single-CTA iterate");
+        if (rep) return fill_report(plan, K, rep, s);
+        return CDV_OK;
+    }
     if (o.use_graph) {
         cdv_plan::Key k{Y, X, K, o.x0_policy, o.max_halvings, o.max_rejects, delta0, o.beta};
         const bool same = plan->key_valid && memcmp(&k, &plan->key, sizeof k) == 0;

@@ -109,6 +109,24 @@ size_t grad_psf_partials(const GradPsfPlan& g);
 cudaError_t launch_grad_psf(const GradPsfPlan& g, const float* X, const float* dY, double* partial,
                             float* dH, cudaStream_t s);
 
+// Whole-run kernel for problems that fit in one SM's shared memory (small.cu).
+struct SmallRun {
+    int64_t m[3];
+    int p[3];
+    const float* y;
+    float* x;
+    const float* h;
+    IterState* st;
+    double* f_hist;
+    double* d_hist;
+    int hist_cap, K, x0_policy, max_halvings, max_rejects;
+    double delta0, beta;
+    const double* absum;
+};
+bool small_supported(const int64_t* m, const int* p);
+size_t small_smem_bytes(const int64_t* m, const int* p);
+cudaError_t small_iterate(const SmallRun& r, cudaStream_t s, bool prepare);
+
 // Message returned by cdv_last_error() on this host thread (capi.cu).
 void set_last_error(const char* msg);
 

@@ -255,9 +255,12 @@ conv_fp32_kernel(const ConvLaunch L, const int ntx, const int nty, const int til
         }
     }
 
-    // Epilogue.
-    double loc = 0.0;
+    // Epilogue.  Per-element arithmetic in FP32 (FP64 runs at a small fraction of
+    // the FP32 rate on this GPU); each thread's squares are summed in FP32 over
+    // its <= 32 outputs and the block and grid sums are FP64.
+    float loc = 0.f;
     const bool row_ok = active && s2 < G.b2;
+    const float deltaf = (float)delta;
 #pragma unroll
     for (int i = 0; i < T1; i++) {
         const int64_t s1 = S1 + i;
@@ -276,7 +279,7 @@ conv_fp32_kernel(const ConvLaunch L, const int ntx, const int nty, const int til
             case ROLE_FWD_TRIAL: {
                 const float rr = v - L.ctx.y[idx];
                 out[idx] = rr;
-                loc = fma((double)rr, (double)rr, loc);
+                loc = fmaf(rr, rr, loc);
                 break;
             }
             case ROLE_ADJ_TRIAL: {
@@ -288,11 +291,10 @@ conv_fp32_kernel(const ConvLaunch L, const int ntx, const int nty, const int til
                     gg = L.ctx.g[idx];
                 }
                 const float xo = L.ctx.x[cur][idx];
-                const double xn_d = fmax((double)xo - delta * (double)gg, 0.0);
-                const float xn = (float)xn_d;
+                const float xn = fmaxf(fmaf(-deltaf, gg, xo), 0.f);
                 L.ctx.x[cur ^ 1][idx] = xn;
-                const double d = (double)xn - (double)xo;
-                loc = fma(d, d, loc);
+                const float d = xn - xo;
+                loc = fmaf(d, d, loc);
                 break;
             }
             case ROLE_RL_RATIO: {
@@ -312,7 +314,7 @@ conv_fp32_kernel(const ConvLaunch L, const int ntx, const int nty, const int til
         }
     }
     if (role == ROLE_FWD_INIT || role == ROLE_FWD_TRIAL || role == ROLE_ADJ_TRIAL) {
-        const double t = block_sum_f64(loc, s_red);
+        const double t = block_sum_f64((double)loc, s_red);
         if (tid == 0) {
             double* part = (role == ROLE_ADJ_TRIAL) ? L.ctx.part_m : L.ctx.part_f;
             part[blockIdx.y * gridDim.x + blockIdx.x] = t;

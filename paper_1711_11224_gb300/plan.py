@@ -125,7 +125,7 @@ class Plan:
 
     # -- iteration ------------------------------------------------------
     @staticmethod
-    def opts(x0="given", delta0=None, beta=0.5, max_halvings=20, max_rejects=16, use_graph=True):
+    def opts(x0="given", delta0=None, beta=0.5, max_halvings=20, max_rejects=16, use_graph=True, path="auto"):
         o = B.IterOpts()
         B.load().cdv_iter_opts_default(ctypes.byref(o))
         o.x0_policy = B.X0[x0]
@@ -134,6 +134,7 @@ class Plan:
         o.max_halvings = int(max_halvings)
         o.max_rejects = int(max_rejects)
         o.use_graph = 1 if use_graph else 0
+        o.path = B.PATHS[path]
         return o
 
     def _report(self, K, want):

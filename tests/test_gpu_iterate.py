@@ -139,3 +139,38 @@ def test_richardson_lucy_matches_oracle():
         Xg = X.cpu().numpy()
     ref = oracle.richardson_lucy(P.Y, P.H, X0, 10)
     assert rel_l2(Xg, ref) <= TOL_ITER
+
+
+@pytest.mark.parametrize("path", ["small", "general"])
+def test_blobs2d_both_paths(path):
+    """The single-CTA path (whole run in one launch) and the general path both match the oracle."""
+    P = synth.blobs2d()
+    _check(P, P.K, path=path)
+
+
+def test_small_path_3d_backtracking_and_policies():
+    from paper_1711_11224_gb300 import Plan
+    P = synth.scaled_fil3d((4, 16, 24), (3, 5, 7), K=12)
+    d0 = 6.0 / oracle.lipschitz(P.H)
+    Xs, rs = _run(P, 12, delta0=d0, max_rejects=200, path="small")
+    Xg, rg = _run(P, 12, delta0=d0, max_rejects=200, path="general")
+    ref = oracle.iterate(P.Y, P.H, oracle.x0_crop(P.Y, P.p), 12, delta0=d0)
+    assert rs["accepted"] == rg["accepted"] == ref["accepted"] == 12
+    assert rs["rejected"] == rg["rejected"] == ref["rejected"]
+    assert rel_l2(Xs, ref["X"]) <= TOL_ITER and rel_l2(Xg, ref["X"]) <= TOL_ITER
+    np.testing.assert_allclose(rs["f"], ref["f"], rtol=1e-5)
+    assert rs["gmac"] == pytest.approx(rg["gmac"])
+    with Plan(P.m, P.p) as pl:
+        pl.set_psf(_dev(P.H))
+        X, rep = pl.iterate(_dev(P.Y), K=0, x0="crop", path="small")
+        np.testing.assert_array_equal(X.cpu().numpy(), oracle.x0_crop(P.Y, P.p).astype(np.float32))
+        X, rep = pl.iterate(_dev(P.Y), _dev(np.ones(P.m)), K=3, x0="zero", path="small")
+        assert rel_l2(X.cpu().numpy(), oracle.iterate(P.Y, P.H, np.zeros(P.m), 3)["X"]) <= TOL_ITER
+
+
+def test_small_path_rejects_large_problem():
+    from paper_1711_11224_gb300 import CdvError, Plan
+    with Plan((64, 64, 64), (1, 1, 1)) as pl:
+        pl.set_psf(_dev(np.ones((3, 3, 3)) / 27))
+        with pytest.raises(CdvError, match="UNSUPPORTED"):
+            pl.iterate(_dev(np.zeros((66, 66, 66))), K=1, path="small")
