@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+
 #include "cdv_internal.h"
 
 using namespace cdv;
@@ -74,6 +76,14 @@ struct cdv_plan {
     double* d_hist = nullptr;
     GradPsfPlan gp{};
     double* gp_part = nullptr;
+    // tensor-core modes
+    TcArgs tcf{}, tca{};            // forward / adjoint launch templates
+    void* xsh[2][2] = {};           // BF16/TF32 shadows of the iterates [buffer][part]
+    void* rsh[2][2] = {};           // shadows of the residuals
+    int64_t pitch_x = 0, pitch_r = 0;
+    CUtensorMap map_x[4], map_r[4]; // hi0, lo0, hi1, lo1
+    int* dev_err = nullptr;
+    bool tc() const { return mode != CDV_MODE_FP32; }
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -111,6 +121,129 @@ struct cdv_plan {
         cap = nullptr;
     }
 };
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+static int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// Launch template of the tensor-core engine for one direction.
+static bool tc_config(const cdv_plan* P, const ConvGeom& g, bool fwd, TcArgs& t)
+{
+    const int ept = (P->mode == CDV_MODE_TF32) ? 4 : 8;
+    t = TcArgs{};
+    t.g = g;
+    t.kind = (int)P->mode;
+    t.nprec = (P->mode == CDV_MODE_SPLIT_BF16X3) ? 2 : 1;
+    const int off = g.o3 - (g.q3 - 1);
+    t.e = ((off % ept) + ept) % ept;
+    t.K = (t.e + g.q3 + 15 + 15) / 16 * 16;
+    t.kchunks = t.K / ept;
+    t.P = 8;
+    t.MT = 2;
+    t.rows = (128 * t.MT + g.q2 - 1 + 15) / 16 * 16;
+    t.tiles1 = ceil_div(g.b1, t.P);
+    t.tiles2 = ceil_div(g.b2, 128 * t.MT);
+    t.tiles3 = ceil_div(g.b3, 16);
+    const int64_t grid = (int64_t)t.tiles1 * t.tiles2 * t.tiles3;
+    if (grid > (1LL << 31) - 1 || t.rows / 2 > 256 || t.K > 256) return false;
+    t.grid = (int)grid;
+    t.tmem_cols = 512;
+    t.sh_pitch = fwd ? P->pitch_r : P->pitch_x;
+    t.err = P->dev_err;
+    // deepest template-tile ring that fits: each stage is one template row of one input plane
+    t.na = 2;
+    t.ns = 16;
+    while (tc_smem_bytes(t) > 220 * 1024 && t.ns > 2) t.ns--;
+    if (tc_smem_bytes(t) > 220 * 1024) t.na = 1;
+    return tc_smem_bytes(t) <= 220 * 1024;
+}
+
+static cudaError_t make_map(CUtensorMap* m, const cdv_plan* P, void* base, int64_t d1, int64_t d2, int64_t d3,
+                            int64_t pitch)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const bool tf = P->mode == CDV_MODE_TF32;
+    const int es = tf ? 4 : 2, ept = tf ? 4 : 8;
+    cuuint64_t dims[3] = {(cuuint64_t)d3, (cuuint64_t)d2, (cuuint64_t)d1};
+    cuuint64_t strides[2] = {(cuuint64_t)(pitch * es), (cuuint64_t)(d2 * pitch * es)};
+    cuuint32_t box[3] = {(cuuint32_t)ept, (cuuint32_t)(P->tcf.rows / 2), 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(m, tf ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims,
+                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Tensor-core state of a plan: launch templates, shadows, tensor maps, tile storage.
+static cudaError_t tc_setup(cdv_plan* P)
+{
+    cudaError_t e = tc_prepare((int)P->mode);
+    if (e != cudaSuccess) return e;
+    const int es = (P->mode == CDV_MODE_TF32) ? 4 : 2;
+    const int nprec = (P->mode == CDV_MODE_SPLIT_BF16X3) ? 2 : 1;
+    P->pitch_x = (P->m[2] + 7) / 8 * 8;
+    P->pitch_r = (P->gf.b3 + 7) / 8 * 8;
+    if (!tc_config(P, P->gf, true, P->tcf) || !tc_config(P, P->ga, false, P->tca)) return cudaErrorNotSupported;
+    const size_t xs = (size_t)P->m[0] * P->m[1] * P->pitch_x * es;
+    const size_t rs = (size_t)P->gf.b1 * P->gf.b2 * P->pitch_r * es;
+    for (int b = 0; b < 2; b++)
+        for (int p = 0; p < 2; p++) {
+            if (p < nprec) {
+                if ((e = P->alloc((unsigned char**)&P->xsh[b][p], xs)) != cudaSuccess) return e;
+                if ((e = P->alloc((unsigned char**)&P->rsh[b][p], rs)) != cudaSuccess) return e;
+            } else {
+                P->xsh[b][p] = P->xsh[b][0];
+                P->rsh[b][p] = P->rsh[b][0];
+            }
+        }
+    // Toeplitz tiles: per part, q2 x kchunks x (q1*16 rows) x 16 bytes
+    for (int d = 0; d < 2; d++) {
+        TcArgs& t = d ? P->tca : P->tcf;
+        const size_t bytes = (size_t)P->q[1] * t.kchunks * P->q[0] * 16 * 16;
+        for (int p = 0; p < 2; p++) {
+            void* ptr = nullptr;
+            if (p < nprec) {
+                if ((e = P->alloc((unsigned char**)&ptr, bytes)) != cudaSuccess) return e;
+            } else {
+                ptr = const_cast<void*>(t.bt[0]);
+            }
+            t.bt[p] = ptr;
+        }
+    }
+    for (int b = 0; b < 2; b++)
+        for (int p = 0; p < 2; p++) {
+            if ((e = make_map(&P->map_x[2 * b + p], P, P->xsh[b][p], P->m[0], P->m[1], P->m[2], P->pitch_x)) != cudaSuccess)
+                return e;
+            if ((e = make_map(&P->map_r[2 * b + p], P, P->rsh[b][p], P->gf.b1, P->gf.b2, P->gf.b3, P->pitch_r)) !=
+                cudaSuccess)
+                return e;
+        }
+    for (int b = 0; b < 2; b++) {
+        P->tcf.sh_out_hi[b] = P->rsh[b][0];
+        P->tcf.sh_out_lo[b] = P->rsh[b][1];
+        P->tca.sh_out_hi[b] = P->xsh[b][0];
+        P->tca.sh_out_lo[b] = P->xsh[b][1];
+    }
+    P->nparts = std::max(P->nparts, std::max(P->tcf.grid, P->tca.grid));
+    return cudaSuccess;
+}
 
 extern "C" {
 
@@ -156,7 +289,6 @@ cdv_status cdv_plan_create(cdv_plan** out, int n, const int64_t* m, const int32_
     if (n < 1 || n > 3) return fail(CDV_ERR_SHAPE, "n = %d, must be 1, 2 or 3", n);
     if (mode != CDV_MODE_FP32 && mode != CDV_MODE_BF16 && mode != CDV_MODE_TF32 && mode != CDV_MODE_SPLIT_BF16X3)
         return fail(CDV_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
-    if (mode != CDV_MODE_FP32) return fail(CDV_ERR_UNSUPPORTED, "mode %d has no kernel in this build", (int)mode);
     for (int i = 0; i < n; i++) {
         if (m[i] < 1) return fail(CDV_ERR_SHAPE, "m[%d] = %lld < 1", i, (long long)m[i]);
         if (p[i] < 0) return fail(CDV_ERR_SHAPE, "p[%d] = %d < 0", i, (int)p[i]);
@@ -182,7 +314,7 @@ cdv_status cdv_plan_create(cdv_plan** out, int n, const int64_t* m, const int32_
     P->nx = P->m[0] * P->m[1] * P->m[2];
     P->ny = (P->m[0] + 2 * P->p[0]) * (P->m[1] + 2 * P->p[1]) * (P->m[2] + 2 * P->p[2]);
     P->nh = (int64_t)P->q[0] * P->q[1] * P->q[2];
-    if (!conv_fp32_supported(P->q[2])) {
+    if (mode == CDV_MODE_FP32 && !conv_fp32_supported(P->q[2])) {
         delete P;
         return fail(CDV_ERR_UNSUPPORTED, "template width %d along the contiguous axis: this build supports odd 1..31",
                     P->q[2]);
@@ -199,7 +331,7 @@ cdv_status cdv_plan_create(cdv_plan** out, int n, const int64_t* m, const int32_
                         std::max(1, (152 * 4 + P->q[0] - 1) / P->q[0])};
 
     cudaError_t e = cudaGetDevice(&P->device);
-    if (e == cudaSuccess) e = conv_fp32_prepare(P->q[2]);
+    if (e == cudaSuccess && conv_fp32_supported(P->q[2])) e = conv_fp32_prepare(P->q[2]);
     if (e == cudaSuccess) e = grad_psf_prepare();
     if (e == cudaSuccess && small_supported(P->m, P->p)) {
         SmallRun r{};
@@ -210,6 +342,17 @@ cdv_status cdv_plan_create(cdv_plan** out, int n, const int64_t* m, const int32_
         e = small_iterate(r, nullptr, true);
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = P->alloc(&P->dev_err, 1);
+    if (e == cudaSuccess) e = cudaMemset(P->dev_err, 0, sizeof(int));
+    if (e == cudaSuccess && P->tc()) {
+        e = tc_setup(P);
+        if (e == cudaErrorNotSupported) {
+            cudaGetLastError();
+            P->release();
+            delete P;
+            return fail(CDV_ERR_UNSUPPORTED, "no tensor-core kernel for this size (template rows > 129 or too wide)");
+        }
+    }
     if (e == cudaSuccess) e = P->alloc(&P->H, P->nh);
     if (e == cudaSuccess) e = P->alloc(&P->Ht, P->nh);
     if (e == cudaSuccess) e = P->alloc(&P->absum, 1);
@@ -251,6 +394,15 @@ cdv_status cdv_plan_set_psf(cdv_plan* plan, const float* H, void* stream)
     CDV_CUDA(cudaMemcpyAsync(plan->H, H, plan->nh * sizeof(float), cudaMemcpyDeviceToDevice, s), "copy H");
     CDV_CUDA(launch_flip(plan->H, plan->Ht, plan->q[0], plan->q[1], plan->q[2], s), "flip H");
     CDV_CUDA(launch_abs_sum(plan->H, plan->nh, plan->absum, s), "sum |H|");
+    if (plan->tc()) {
+        const int q3 = plan->q[2];
+        CDV_CUDA(tc_build_btiles(plan->H, plan->q[0], plan->q[1], q3, q3 - 1 + plan->tcf.e, plan->tcf.K,
+                                 (int)plan->mode, const_cast<void*>(plan->tcf.bt[0]),
+                                 const_cast<void*>(plan->tcf.bt[1]), s), "Toeplitz tiles (forward)");
+        CDV_CUDA(tc_build_btiles(plan->Ht, plan->q[0], plan->q[1], q3, q3 - 1 + plan->tca.e, plan->tca.K,
+                                 (int)plan->mode, const_cast<void*>(plan->tca.bt[0]),
+                                 const_cast<void*>(plan->tca.bt[1]), s), "Toeplitz tiles (adjoint)");
+    }
     plan->has_psf = true;
     return CDV_OK;
 }
@@ -279,6 +431,23 @@ static cdv_status run_conv(cdv_plan* P, bool fwd, int batch, const float* in, fl
     if (!in || !out) return fail(CDV_ERR_INVALID_ARG, "NULL array");
     if (batch < 1 || batch > 65535) return fail(CDV_ERR_INVALID_ARG, "batch = %d", batch);
     if (!P->has_psf) return fail(CDV_ERR_NO_PSF, "no template set");
+    if (P->tc()) {
+        const ConvGeom& g = fwd ? P->gf : P->ga;
+        for (int b = 0; b < batch; b++) {
+            const float* src = in + (int64_t)b * (fwd ? P->nx : P->ny);
+            if (fwd)
+                CDV_CUDA(tc_shadow(src, g.a1 * g.a2, g.a3, P->pitch_x, (int)P->mode, P->xsh[0][0], P->xsh[0][1], s),
+                         "input shadow");
+            else
+                CDV_CUDA(tc_shadow(src, g.a1 * g.a2, g.a3, P->pitch_r, (int)P->mode, P->rsh[0][0], P->rsh[0][1], s),
+                         "input shadow");
+            TcArgs t = fwd ? P->tcf : P->tca;
+            t.role = ROLE_PLAIN;
+            t.out = out + (int64_t)b * (fwd ? P->ny : P->nx);
+            CDV_CUDA(tc_launch(t, fwd ? P->map_x : P->map_r, s), fwd ? "forward (tensor cores)" : "adjoint (tensor cores)");
+        }
+        return CDV_OK;
+    }
     ConvLaunch L{};
     L.g = fwd ? P->gf : P->ga;
     L.in = in;
@@ -332,8 +501,34 @@ static IterCtx make_ctx(cdv_plan* P, const float* Y, float* X)
     return c;
 }
 
+static cdv_status enqueue_run_tc(cdv_plan* P, const float* Y, float* X, int K, const cdv_iter_opts& o, cudaStream_t s)
+{
+    const IterCtx c = make_ctx(P, Y, X);
+    CDV_CUDA(launch_x0(o.x0_policy, X, Y, P->m[0], P->m[1], P->m[2], P->p[0], P->p[1], P->p[2], s), "x0");
+    CDV_CUDA(tc_shadow(X, P->m[0] * P->m[1], P->m[2], P->pitch_x, (int)P->mode, P->xsh[0][0], P->xsh[0][1], s),
+             "x0 shadow");
+    CDV_CUDA(launch_state_init(P->st, o.delta0, P->absum, o.beta, o.max_halvings, o.max_rejects, K, kHistCap, s), "state");
+    TcArgs F = P->tcf, A = P->tca;
+    F.ctx = c;
+    A.ctx = c;
+    F.role = ROLE_FWD_INIT;
+    CDV_CUDA(tc_launch(F, P->map_x, s), "forward (initial, tensor cores)");
+    CDV_CUDA(launch_decide(c, F.grid, 0, 1, s), "decide (initial)");
+    F.role = ROLE_FWD_TRIAL;
+    A.role = ROLE_ADJ_TRIAL;
+    const int slots = K + o.max_rejects;
+    for (int i = 0; i < slots && K > 0; i++) {
+        CDV_CUDA(tc_launch(A, P->map_r, s), "adjoint trial (tensor cores)");
+        CDV_CUDA(tc_launch(F, P->map_x, s), "forward trial (tensor cores)");
+        CDV_CUDA(launch_decide(c, F.grid, A.grid, 0, s), "decide");
+    }
+    CDV_CUDA(launch_finalize(c, P->nx, s), "finalize");
+    return CDV_OK;
+}
+
 static cdv_status enqueue_run(cdv_plan* P, const float* Y, float* X, int K, const cdv_iter_opts& o, cudaStream_t s)
 {
+    if (P->tc()) return enqueue_run_tc(P, Y, X, K, o, s);
     const IterCtx c = make_ctx(P, Y, X);
     CDV_CUDA(launch_x0(o.x0_policy, X, Y, P->m[0], P->m[1], P->m[2], P->p[0], P->p[1], P->p[2], s), "x0");
     CDV_CUDA(launch_state_init(P->st, o.delta0, P->absum, o.beta, o.max_halvings, o.max_rejects, K, kHistCap, s), "state");
@@ -365,9 +560,11 @@ static cdv_status fill_report(cdv_plan* P, int K, cdv_iter_report* rep, cudaStre
     CDV_CUDA(cudaStreamSynchronize(s), "iterate sync");
     IterState st;
     CDV_CUDA(cudaMemcpy(&st, P->st, sizeof st, cudaMemcpyDeviceToHost), "read state");
+    int derr = 0;
+    CDV_CUDA(cudaMemcpy(&derr, P->dev_err, sizeof(int), cudaMemcpyDeviceToHost), "read error word");
     rep->accepted = st.accepted;
     rep->rejected = st.rejected;
-    rep->status = st.status;
+    rep->status = derr ? derr : st.status;
     rep->trials = st.trials;
     double f0 = 0.0;
     CDV_CUDA(cudaMemcpy(&f0, P->f_hist, sizeof(double), cudaMemcpyDeviceToHost), "read f0");
@@ -397,7 +594,7 @@ cdv_status cdv_iterate(cdv_plan* plan, const float* Y, float* X, int K, const cd
     if (o.path < CDV_PATH_AUTO || o.path > CDV_PATH_SMALL) return fail(CDV_ERR_INVALID_ARG, "path = %d", o.path);
     const double delta0 = o.delta0 > 0.0 ? o.delta0 : 0.0;
     cudaStream_t s = (cudaStream_t)stream;
-    const bool small_ok = small_supported(plan->m, plan->p);
+    const bool small_ok = !plan->tc() && small_supported(plan->m, plan->p);
     if (o.path == CDV_PATH_SMALL && !small_ok)
         return fail(CDV_ERR_UNSUPPORTED, "problem does not fit the single-CTA path (%zu bytes of shared memory)",
                     small_smem_bytes(plan->m, plan->p));
@@ -478,6 +675,7 @@ cdv_status cdv_iterate_host(cdv_plan* plan, const float* Y_host, float* X_host, 
 cdv_status cdv_richardson_lucy(cdv_plan* plan, const float* Y, float* X, int K, void* stream)
 {
     if (!plan || !Y || !X) return fail(CDV_ERR_INVALID_ARG, "NULL argument");
+    if (plan->tc()) return fail(CDV_ERR_UNSUPPORTED, "Richardson-Lucy runs in CDV_MODE_FP32 only");
     if (K < 0) return fail(CDV_ERR_INVALID_ARG, "K = %d", K);
     if (!plan->has_psf) return fail(CDV_ERR_NO_PSF, "no template set");
     cudaStream_t s = (cudaStream_t)stream;
@@ -512,6 +710,12 @@ cdv_status cdv_plan_sync_status(cdv_plan* plan, void* stream)
     if (!plan) return fail(CDV_ERR_INVALID_ARG, "plan is NULL");
     CDV_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "sync");
     CDV_CUDA(cudaGetLastError(), "pending error");
+    int derr = 0;
+    CDV_CUDA(cudaMemcpy(&derr, plan->dev_err, sizeof(int), cudaMemcpyDeviceToHost), "read error word");
+    if (derr) {
+        CDV_CUDA(cudaMemset(plan->dev_err, 0, sizeof(int)), "clear error word");
+        return fail((cdv_status)derr, "device-side error recorded by a kernel");
+    }
     return CDV_OK;
 }
 

@@ -127,6 +127,38 @@ bool small_supported(const int64_t* m, const int* p);
 size_t small_smem_bytes(const int64_t* m, const int* p);
 cudaError_t small_iterate(const SmallRun& r, cudaStream_t s, bool prepare);
 
+// Tensor-core engine (conv_tc.cu).  One launch = one convolution over the
+// whole volume; the input is read through TMA from BF16/TF32 shadow copies
+// in a padded layout, the FP32 output and the shadows of the output are
+// written by the epilogue.
+struct TcArgs {
+    ConvGeom g;
+    int role, kind, nprec;
+    int e;               // window pad: K index 0 is input column S3 + o3 - (q3-1) - e
+    int K;               // window length (elements), multiple of 16
+    int kchunks;         // 16-byte chunks along K
+    int P;               // output planes per CTA (N of one MMA = 16 x planes)
+    int MT;              // 128-row M tiles per CTA
+    int rows;            // staged input rows (>= 128*MT + q2 - 1), two TMA boxes of rows/2
+    int na, ns;          // input-plane buffers, template-tile stages
+    int tiles1, tiles2, tiles3, grid;
+    unsigned tmem_cols;
+    int64_t sh_pitch;    // row pitch of the output shadows
+    float* out;          // ROLE_PLAIN output
+    const void* bt[2];   // Toeplitz tiles [part][j2][K chunk][j1*16 + n][16 bytes]
+    void* sh_out_hi[2];
+    void* sh_out_lo[2];
+    int* err;            // device error word
+    IterCtx ctx;
+};
+size_t tc_smem_bytes(const TcArgs& t);
+cudaError_t tc_prepare(int kind);
+cudaError_t tc_launch(const TcArgs& t, const struct CUtensorMap_st* maps, cudaStream_t s);
+cudaError_t tc_build_btiles(const float* w, int q1, int q2, int q3, int D, int K, int kind, void* hi, void* lo,
+                            cudaStream_t s);
+cudaError_t tc_shadow(const float* src, int64_t a1a2, int64_t a3, int64_t pitch, int kind, void* hi, void* lo,
+                      cudaStream_t s);
+
 // Message returned by cdv_last_error() on this host thread (capi.cu).
 void set_last_error(const char* msg);
 

@@ -1,0 +1,596 @@
+// Tensor-core (tcgen05) direct convolution: implicit GEMM with a Toeplitz
+// operand along the contiguous axis.
+//
+// For the generic operator out[s] = sum_j w[j] in[s + o - j] (forward:
+// in = X, o = 0, w = H; adjoint: in = R, o = 2p, w = H~), fix the template
+// plane j1 and row j2.  The sum over j3 for 16 consecutive output columns is
+// an input window of K columns times a banded Toeplitz matrix
+// T_{j1,j2}[k, n] = w[j1, j2, n + D - k].  With 128 consecutive output rows
+// as M this is one tcgen05.mma per 16-wide K step:
+//     D_{s1}[row, n] += A_{u, j2}[row, k] * T_{s1+o1-u, j2}[k, n]
+// where A_{u, j2} is input plane u read at rows shifted by j2.
+//
+// Shapes chosen for the tensor pipe (an M128 x K16 MMA costs about
+// max(46, N/2) cycles, so N must be large):
+//  * N = 16 x (output planes): one input plane u and template row j2 feed the
+//    CTA's P = 8 output planes through Toeplitz tiles of consecutive j1, which
+//    are stored side by side ([j2][K chunk][j1*16 + n]), so one MMA with
+//    N = 16 x (planes in range) updates all of them.
+//  * M = 2 x 128 rows per CTA: both M tiles share each staged B stage.
+//  * The row shift j2 is a 16-byte shift of the shared-memory descriptor of
+//    one TMA-staged tile of plane u (K-major, no swizzle: core matrices of
+//    8 rows x 16 bytes, rows 16 bytes apart), so the tile serves all q2 rows.
+//  * Two-level accumulation: the contribution of each input plane goes to a
+//    fresh TMEM partial (two buffers), which epilogue warps add into FP32
+//    register totals while the MMAs of the next plane run.  One TMEM
+//    accumulator over all q1*q2 template rows drifts (the tensor core's FP32
+//    accumulation truncates): 1e-4 relative for a 31x31x21 template.
+//
+// Warp roles (320 threads):
+//   warp 0      TMA producer: per input plane, the A tile (per 16-byte K chunk
+//               two boxes of rows/2 rows, zero-filled outside the volume) and,
+//               per template row, the Toeplitz tiles of the planes in range
+//               (bulk copies through a 4-stage ring).
+//   warp 1      MMA issuer (one thread): per (j2, K step, M tile) one MMA,
+//               three for split-BF16x3 (hi*hi, hi*lo, lo*hi); tcgen05.commit
+//               releases ring stages and hands each plane's partial to the
+//               epilogue.
+//   warps 2-9   epilogue, one warpgroup per M tile, one output row per thread:
+//               drains the partials, then the fused epilogue of the FP32
+//               engine plus the BF16/TF32 shadows the next convolution reads.
+// Every wait is bounded (about 0.5 s).  A wait that runs out records
+// CDV_ERR_TIMEOUT in the device error word; the CTA stops issuing work, waits
+// for its own copies and MMAs, frees its TMEM and exits.  CTAs that start
+// after an error has been recorded skip their work.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "cdv_internal.h"
+
+namespace cdv {
+
+namespace {
+
+constexpr int kM = 128;
+constexpr int kN = 16;
+constexpr int kP = 8;          // output planes per CTA
+constexpr int kMT = 2;         // M tiles per CTA
+constexpr int kThreads = 320;
+
+__device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t sdesc(unsigned addr, unsigned lbo, unsigned sbo)
+{
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+// Bounded wait for the phase of the given parity; false after ~1e9 cycles (~0.5 s).
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity)
+{
+    const long long t0 = clock64();
+    for (;;) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > 1000000000ll) return false;
+    }
+}
+__device__ __forceinline__ void tma3(unsigned dst, const CUtensorMap* map, int x, int y, int z, unsigned bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(dst),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+template <int KIND>
+__device__ __forceinline__ void mma(unsigned d, uint64_t a, uint64_t b, unsigned idesc, unsigned acc)
+{
+    if (KIND == CDV_MODE_TF32)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    else
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mbar_arrive(unsigned bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mma_commit(unsigned bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float* v)
+{
+    unsigned r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// Shadow value(s) of an FP32 result for the next tensor-core convolution.
+template <int KIND>
+__device__ __forceinline__ void store_shadow(void* hi, void* lo, int64_t i, float v)
+{
+    if (KIND == CDV_MODE_TF32) {
+        unsigned t;
+        asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(t) : "f"(v));
+        reinterpret_cast<unsigned*>(hi)[i] = t;
+    } else {
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        reinterpret_cast<__nv_bfloat16*>(hi)[i] = h;
+        if (KIND == CDV_MODE_SPLIT_BF16X3)
+            reinterpret_cast<__nv_bfloat16*>(lo)[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+}
+
+}  // namespace
+
+// Shared-memory layout of one CTA (bytes).
+struct TcSmem {
+    size_t a_bytes, b_bytes, off_b, off_bar, total;
+    __host__ __device__ static TcSmem make(const TcArgs& t)
+    {
+        TcSmem s;
+        s.a_bytes = (size_t)t.kchunks * t.rows * 16;              // one part of one input plane
+        s.b_bytes = (size_t)t.kchunks * t.P * kN * 16;           // one part of one ring stage
+        s.off_b = (size_t)t.na * t.nprec * s.a_bytes;
+        s.off_bar = s.off_b + (size_t)t.ns * t.nprec * s.b_bytes;
+        s.total = s.off_bar + 512;
+        return s;
+    }
+};
+
+size_t tc_smem_bytes(const TcArgs& t) { return TcSmem::make(t).total + 1024; }
+
+template <int KIND>
+__global__ void __launch_bounds__(kThreads, 1)
+conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtensorMap mh0,
+               const __grid_constant__ CUtensorMap ml0, const __grid_constant__ CUtensorMap mh1,
+               const __grid_constant__ CUtensorMap ml1)
+{
+    constexpr int NPREC = (KIND == CDV_MODE_SPLIT_BF16X3) ? 2 : 1;
+    constexpr int EPT = (KIND == CDV_MODE_TF32) ? 4 : 8;       // elements per 16-byte K chunk
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const TcSmem lay = TcSmem::make(T);
+    const ConvGeom& G = T.g;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    int bt = blockIdx.x;
+    const int t3 = bt % T.tiles3;
+    bt /= T.tiles3;
+    const int t2 = bt % T.tiles2;
+    const int t1 = bt / T.tiles2;
+    const int64_t S1 = (int64_t)t1 * kP, S2 = (int64_t)t2 * kM * kMT, S3 = (int64_t)t3 * kN;
+
+    const int role = T.role;
+    int sel = 0, cur = 0;
+    bool do_conv = true;
+    float delta = 0.f;
+    float* out = T.out;
+    const float* xin = nullptr;
+    if (role == ROLE_FWD_INIT || role == ROLE_FWD_TRIAL || role == ROLE_ADJ_TRIAL) {
+        const IterState* st = T.ctx.st;
+        if (st->done) return;
+        cur = st->cur;
+        if (role == ROLE_FWD_INIT) {
+            sel = cur;
+            out = T.ctx.r[cur];
+        } else if (role == ROLE_FWD_TRIAL) {
+            sel = cur ^ 1;
+            out = T.ctx.r[cur ^ 1];
+        } else {
+            sel = cur;
+            out = T.ctx.g;
+            xin = T.ctx.x[cur];
+            delta = (float)st->delta;
+            do_conv = st->need_grad != 0;
+        }
+    }
+    const CUtensorMap* map_hi = sel ? &mh1 : &mh0;
+    const CUtensorMap* map_lo = sel ? &ml1 : &ml0;
+
+    unsigned char* sA = sm;
+    unsigned char* sB = sm + lay.off_b;
+    // barriers: a_full[2] a_empty[2] b_full[16] b_empty[16] acc_full[2] acc_free[2] drain
+    const unsigned bar0 = su32(sm + lay.off_bar);
+    auto A_FULL = [&](int i) { return bar0 + 8u * i; };
+    auto A_EMPTY = [&](int i) { return bar0 + 8u * (2 + i); };
+    auto B_FULL = [&](int i) { return bar0 + 8u * (4 + i); };
+    auto B_EMPTY = [&](int i) { return bar0 + 8u * (20 + i); };
+    auto ACC_FULL = [&](int i) { return bar0 + 8u * (36 + i); };
+    auto ACC_FREE = [&](int i) { return bar0 + 8u * (38 + i); };
+    const unsigned DRAIN = bar0 + 8u * 40;
+    unsigned* tslot = reinterpret_cast<unsigned*>(sm + lay.off_bar + 384);
+    volatile int* sflag = reinterpret_cast<volatile int*>(sm + lay.off_bar + 392);
+
+    // input planes reaching the CTA's output planes [S1, min(S1 + P, b1))
+    const int64_t s1_end = min(S1 + kP, G.b1);
+    const int64_t ulo = max((int64_t)0, S1 + G.o1 - G.q1 + 1);
+    const int64_t uhi = min(G.a1 - 1, s1_end - 1 + G.o1);
+    const bool have_work = do_conv && ulo <= uhi && *(volatile int*)T.err == 0;
+
+    if (tid == 0) {
+        for (int i = 0; i < 38; i++) mbar_init(bar0 + 8u * i, 1);
+        mbar_init(ACC_FREE(0), 8);
+        mbar_init(ACC_FREE(1), 8);
+        mbar_init(DRAIN, 1);
+        *sflag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    const unsigned tcols = T.tmem_cols;
+    if (have_work && warp == 0) {
+        __syncwarp();
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tslot)), "r"(tcols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const unsigned tmem = have_work ? *tslot : 0u;
+
+    const int64_t ws = S3 + G.o3 - (G.q3 - 1) - T.e;             // input column of K index 0
+    const int64_t v0 = S2 + G.o2 - (G.q2 - 1);                    // input row of staged row 0
+    const int half = T.rows / 2;
+    const int ksteps = T.K / (2 * EPT);
+    // output planes of the CTA that input plane u reaches: [ilo, ihi] (relative to S1)
+    auto plane_range = [&](int64_t u, int& ilo, int& ihi) {
+        ilo = (int)max((int64_t)0, u - G.o1 - S1);
+        ihi = (int)min(s1_end - 1 - S1, u - G.o1 + G.q1 - 1 - S1);
+    };
+    auto fail = [&]() {
+        *sflag = 1;
+        atomicExch(T.err, (int)CDV_ERR_TIMEOUT);
+    };
+
+    if (have_work && warp == 0 && lane == 0) {
+        // ---------------- TMA producer
+        int bs = 0, it = 0, nb = 0;
+        unsigned bph = 0;
+        int a_uses[2] = {0, 0};
+        for (int64_t u = ulo; u <= uhi && !*sflag; ++u, ++it) {
+            const int ab = it % T.na;
+            if (!mbar_wait(A_EMPTY(ab), (unsigned)(((it / T.na) & 1) ^ 1))) { fail(); break; }
+            mbar_expect_tx(A_FULL(ab), (unsigned)(NPREC * lay.a_bytes));
+            a_uses[ab] = it / T.na + 1;
+            for (int p = 0; p < NPREC; p++) {
+                const CUtensorMap* mp = p ? map_lo : map_hi;
+                const unsigned dst = su32(sA + ((size_t)ab * NPREC + p) * lay.a_bytes);
+                for (int c = 0; c < T.kchunks; c++)
+                    for (int h = 0; h < 2; h++)
+                        tma3(dst + (unsigned)((c * T.rows + h * half) * 16), mp, (int)(ws + c * EPT), (int)(v0 + h * half),
+                             (int)u, A_FULL(ab));
+            }
+            int ilo, ihi;
+            plane_range(u, ilo, ihi);
+            const int64_t j1lo = S1 + ilo + G.o1 - u;
+            const int nv = ihi - ilo + 1;
+            for (int j2 = 0; j2 < G.q2; j2++) {
+                if (!mbar_wait(B_EMPTY(bs), bph ^ 1)) { fail(); break; }
+                mbar_expect_tx(B_FULL(bs), (unsigned)(NPREC * T.kchunks * nv * kN * 16));
+                for (int p = 0; p < NPREC; p++) {
+                    const unsigned char* src0 = reinterpret_cast<const unsigned char*>(T.bt[p]);
+                    const unsigned dst = su32(sB + ((size_t)bs * NPREC + p) * lay.b_bytes);
+                    for (int c = 0; c < T.kchunks; c++) {
+                        const size_t row = ((size_t)j2 * T.kchunks + c) * G.q1 * kN + (size_t)j1lo * kN;
+                        bulk_g2s(dst + (unsigned)(c * T.P * kN * 16), src0 + row * 16, (unsigned)(nv * kN * 16), B_FULL(bs));
+                    }
+                }
+                ++nb;
+                if (++bs == T.ns) { bs = 0; bph ^= 1; }
+            }
+        }
+        // make sure every copy this thread issued has landed before the CTA may exit
+        for (int ab = 0; ab < T.na; ab++)
+            if (a_uses[ab] > 0) mbar_wait(A_FULL(ab), (unsigned)((a_uses[ab] - 1) & 1));
+        for (int k = 0; k < T.ns && k < nb; k++) {
+            const int idx = nb - 1 - k;                           // the last use of each stage
+            mbar_wait(B_FULL(idx % T.ns), (unsigned)((idx / T.ns) & 1));
+        }
+    } else if (have_work && warp == 1 && lane == 0) {
+        // ---------------- MMA issuer
+        const unsigned fmt = (KIND == CDV_MODE_TF32) ? 2u : 1u;
+        const unsigned lbo_a = (unsigned)T.rows * 16, lbo_b = (unsigned)T.P * kN * 16;
+        int bs = 0, it = 0;
+        unsigned bph = 0;
+        bool ok = true;
+        for (int64_t u = ulo; u <= uhi && ok && !*sflag; ++u, ++it) {
+            const int b = it & 1;
+            if (it >= 2 && !mbar_wait(ACC_FREE(b), (unsigned)(((it >> 1) - 1) & 1))) { ok = false; break; }
+            const int ab = it % T.na;
+            if (!mbar_wait(A_FULL(ab), (unsigned)((it / T.na) & 1))) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            int ilo, ihi;
+            plane_range(u, ilo, ihi);
+            const unsigned n = (unsigned)(kN * (ihi - ilo + 1));
+            const unsigned idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((n >> 3) << 17) | ((unsigned)(kM >> 4) << 24);
+            const unsigned a_hi = su32(sA + ((size_t)ab * NPREC + 0) * lay.a_bytes);
+            const unsigned a_lo = su32(sA + ((size_t)ab * NPREC + (NPREC - 1)) * lay.a_bytes);
+            for (int j2 = 0; j2 < G.q2; j2++) {
+                if (!mbar_wait(B_FULL(bs), bph)) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const unsigned b_hi = su32(sB + ((size_t)bs * NPREC + 0) * lay.b_bytes);
+                const unsigned b_lo = su32(sB + ((size_t)bs * NPREC + (NPREC - 1)) * lay.b_bytes);
+                const unsigned arow = (unsigned)(G.q2 - 1 - j2) * 16u;
+                for (int k = 0; k < ksteps; k++) {
+                    const uint64_t bd_hi = sdesc(b_hi + 2u * k * lbo_b, lbo_b, 128);
+                    const uint64_t bd_lo = sdesc(b_lo + 2u * k * lbo_b, lbo_b, 128);
+                    for (int mt = 0; mt < kMT; mt++) {
+                        if (S2 + (int64_t)mt * kM >= G.b2) break;
+                        const unsigned aoff = 2u * k * lbo_a + arow + (unsigned)(mt * kM * 16);
+                        const unsigned d = tmem + (unsigned)(((mt * 2 + b) * T.P + ilo) * kN);
+                        const unsigned acc = (j2 == 0 && k == 0) ? 0u : 1u;   // fresh partial per input plane
+                        const uint64_t ad_hi = sdesc(a_hi + aoff, lbo_a, 128);
+                        mma<KIND>(d, ad_hi, bd_hi, idesc, acc);
+                        if (KIND == CDV_MODE_SPLIT_BF16X3) {
+                            mma<KIND>(d, ad_hi, bd_lo, idesc, 1u);
+                            mma<KIND>(d, sdesc(a_lo + aoff, lbo_a, 128), bd_hi, idesc, 1u);
+                        }
+                    }
+                }
+                mma_commit(B_EMPTY(bs));
+                if (++bs == T.ns) { bs = 0; bph ^= 1; }
+            }
+            if (!ok) break;
+            mma_commit(A_EMPTY(ab));
+            mma_commit(ACC_FULL(b));
+        }
+        if (!ok) fail();
+        mma_commit(DRAIN);                                        // completes when every issued MMA has
+        if (!mbar_wait(DRAIN, 0)) fail();
+    }
+
+    // ---------------- epilogue (warps 2..9): one M tile per warpgroup, one output row per thread
+    float loc = 0.f;
+    if (warp >= 2) {
+        const int mt = (warp - 2) >> 2;
+        const int quarter = warp & 3;
+        const int m = quarter * 32 + lane;
+        const int64_t s2 = S2 + (int64_t)mt * kM + m;
+        const bool tile_ok = S2 + (int64_t)mt * kM < G.b2;
+        float tot[kP][kN];
+#pragma unroll
+        for (int i = 0; i < kP; i++)
+#pragma unroll
+            for (int c = 0; c < kN; c++) tot[i][c] = 0.f;
+        bool ok = true;
+        if (have_work) {
+            int it = 0;
+            for (int64_t u = ulo; u <= uhi; ++u, ++it) {
+                const int b = it & 1;
+                bool w = mbar_wait(ACC_FULL(b), (unsigned)((it >> 1) & 1));
+                w = __all_sync(0xffffffffu, w && !*sflag);
+                if (!w) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                int ilo, ihi;
+                plane_range(u, ilo, ihi);
+                if (tile_ok) {
+#pragma unroll
+                    for (int i = 0; i < kP; i++) {
+                        if (i < ilo || i > ihi) continue;                 // warp-uniform
+                        float v[kN];
+                        tmem_ld16(tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)(((mt * 2 + b) * T.P + i) * kN), v);
+#pragma unroll
+                        for (int c = 0; c < kN; c++) tot[i][c] += v[c];
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(ACC_FREE(b));
+            }
+        }
+        if (!ok && lane == 0) fail();
+        if (ok && tile_ok && s2 < G.b2) {
+#pragma unroll
+            for (int i = 0; i < kP; i++) {
+                const int64_t s1 = S1 + i;
+                if (s1 >= G.b1) continue;
+#pragma unroll
+                for (int c = 0; c < kN; c++) {
+                    const int64_t s3 = S3 + c;
+                    if (s3 >= G.b3) continue;
+                    const int64_t idx = (s1 * G.b2 + s2) * G.b3 + s3;
+                    const int64_t sidx = (s1 * G.b2 + s2) * T.sh_pitch + s3;
+                    const float v = tot[i][c];
+                    switch (role) {
+                    case ROLE_PLAIN:
+                        out[idx] = v;
+                        break;
+                    case ROLE_FWD_INIT:
+                    case ROLE_FWD_TRIAL: {
+                        const float rr = v - T.ctx.y[idx];
+                        out[idx] = rr;
+                        store_shadow<KIND>(T.sh_out_hi[sel], T.sh_out_lo[sel], sidx, rr);
+                        loc = fmaf(rr, rr, loc);
+                        break;
+                    }
+                    case ROLE_ADJ_TRIAL: {
+                        float gg;
+                        if (do_conv) {
+                            gg = v;
+                            out[idx] = gg;
+                        } else {
+                            gg = T.ctx.g[idx];
+                        }
+                        const float xo = xin[idx];
+                        const float xn = fmaxf(fmaf(-delta, gg, xo), 0.f);
+                        T.ctx.x[cur ^ 1][idx] = xn;
+                        store_shadow<KIND>(T.sh_out_hi[cur ^ 1], T.sh_out_lo[cur ^ 1], sidx, xn);
+                        const float d = xn - xo;
+                        loc = fmaf(d, d, loc);
+                        break;
+                    }
+                    default:
+                        break;
+                    }
+                }
+            }
+        }
+    }
+
+    // ---------------- block partial of the norm, teardown
+    __shared__ double s_red[kThreads / 32];
+    if (role == ROLE_FWD_INIT || role == ROLE_FWD_TRIAL || role == ROLE_ADJ_TRIAL) {
+        double v = (double)loc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) s_red[warp] = v;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0 && (role == ROLE_FWD_INIT || role == ROLE_FWD_TRIAL || role == ROLE_ADJ_TRIAL)) {
+        double t = 0.0;
+        for (int i = 0; i < kThreads / 32; i++) t += s_red[i];
+        double* part = (role == ROLE_ADJ_TRIAL) ? T.ctx.part_m : T.ctx.part_f;
+        part[blockIdx.x] = t;
+    }
+    if (have_work && warp == 0) {
+        __syncwarp();
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tcols));
+    }
+}
+
+// ----------------------------------------------------------------- host side
+
+cudaError_t tc_prepare(int kind)
+{
+    const int smax = 220 * 1024;
+    switch (kind) {
+    case CDV_MODE_BF16:
+        return cudaFuncSetAttribute(conv_tc_kernel<CDV_MODE_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    case CDV_MODE_TF32:
+        return cudaFuncSetAttribute(conv_tc_kernel<CDV_MODE_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    case CDV_MODE_SPLIT_BF16X3:
+        return cudaFuncSetAttribute(conv_tc_kernel<CDV_MODE_SPLIT_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    smax);
+    default:
+        return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t tc_launch(const TcArgs& t, const CUtensorMap* maps, cudaStream_t s)
+{
+    const size_t smem = tc_smem_bytes(t);
+    const dim3 grid((unsigned)t.grid);
+    switch (t.kind) {
+    case CDV_MODE_BF16:
+        conv_tc_kernel<CDV_MODE_BF16><<<grid, kThreads, smem, s>>>(t, maps[0], maps[1], maps[2], maps[3]);
+        break;
+    case CDV_MODE_TF32:
+        conv_tc_kernel<CDV_MODE_TF32><<<grid, kThreads, smem, s>>>(t, maps[0], maps[1], maps[2], maps[3]);
+        break;
+    case CDV_MODE_SPLIT_BF16X3:
+        conv_tc_kernel<CDV_MODE_SPLIT_BF16X3><<<grid, kThreads, smem, s>>>(t, maps[0], maps[1], maps[2], maps[3]);
+        break;
+    default:
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// Toeplitz tiles T_{j1,j2}[k, n] = w[j1, j2, n + D - k] (zero outside [0, q3)),
+// stored K-major for the MMA with the tiles of all j1 side by side along N:
+// part p, row j2, K chunk c: rows j1*16 + n of 16 bytes (EPT elements of K).
+__global__ void tc_btiles_kernel(const float* w, int q1, int q2, int q3, int D, int K, int kind, unsigned char* hi,
+                                 unsigned char* lo)
+{
+    const int ept = (kind == CDV_MODE_TF32) ? 4 : 8;
+    const int kch = K / ept;
+    const int64_t total = (int64_t)q1 * q2 * kN * K;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(i % K);
+        const int n = (int)((i / K) % kN);
+        const int64_t jj = i / ((int64_t)K * kN);                  // j1 * q2 + j2
+        const int j1 = (int)(jj / q2), j2 = (int)(jj % q2);
+        const int j3 = n + D - k;
+        const float v = (j3 >= 0 && j3 < q3) ? w[jj * q3 + j3] : 0.f;
+        const size_t row = ((size_t)j2 * kch + k / ept) * q1 * kN + (size_t)j1 * kN + n;
+        const size_t off = row * 16 + (size_t)(k % ept) * (kind == CDV_MODE_TF32 ? 4 : 2);
+        if (kind == CDV_MODE_TF32) {
+            unsigned t;
+            asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(t) : "f"(v));
+            *reinterpret_cast<unsigned*>(hi + off) = t;
+        } else {
+            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+            *reinterpret_cast<__nv_bfloat16*>(hi + off) = h;
+            if (kind == CDV_MODE_SPLIT_BF16X3)
+                *reinterpret_cast<__nv_bfloat16*>(lo + off) = __float2bfloat16_rn(v - __bfloat162float(h));
+        }
+    }
+}
+
+cudaError_t tc_build_btiles(const float* w, int q1, int q2, int q3, int D, int K, int kind, void* hi, void* lo,
+                            cudaStream_t s)
+{
+    const int64_t total = (int64_t)q1 * q2 * kN * K;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    tc_btiles_kernel<<<blocks, 256, 0, s>>>(w, q1, q2, q3, D, K, kind, (unsigned char*)hi, (unsigned char*)lo);
+    return cudaGetLastError();
+}
+
+// Shadow copy of a dense FP32 volume (a1 x a2 x a3) into the padded layout (row pitch `pitch`).
+__global__ void tc_shadow_kernel(const float* src, int64_t a1a2, int64_t a3, int64_t pitch, int kind, void* hi, void* lo)
+{
+    const int64_t n = a1a2 * a3;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / a3, c = i - r * a3;
+        const int64_t j = r * pitch + c;
+        const float v = src[i];
+        if (kind == CDV_MODE_TF32) {
+            unsigned t;
+            asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(t) : "f"(v));
+            reinterpret_cast<unsigned*>(hi)[j] = t;
+        } else {
+            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+            reinterpret_cast<__nv_bfloat16*>(hi)[j] = h;
+            if (kind == CDV_MODE_SPLIT_BF16X3)
+                reinterpret_cast<__nv_bfloat16*>(lo)[j] = __float2bfloat16_rn(v - __bfloat162float(h));
+        }
+    }
+}
+
+cudaError_t tc_shadow(const float* src, int64_t a1a2, int64_t a3, int64_t pitch, int kind, void* hi, void* lo,
+                      cudaStream_t s)
+{
+    const int64_t n = a1a2 * a3;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+    tc_shadow_kernel<<<blocks, 256, 0, s>>>(src, a1a2, a3, pitch, kind, hi, lo);
+    return cudaGetLastError();
+}
+
+}  // namespace cdv

@@ -1,0 +1,120 @@
+"""Tensor-core (tcgen05) forms against the FP64 oracle.
+
+split-BF16x3 is held to the FP32 bar (relative L2 <= 1e-5 per convolution);
+BF16 and TF32 products are reported against bounds derived from their unit
+roundoff (BF16 2^-9, TF32 2^-12 relative per input, averaged over the taps).
+Integer data are exact in every mode: products and partial sums of small
+integers are representable in BF16/TF32 and FP32.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from _util import TOL_CONV, TOL_ITER, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"split3": TOL_CONV, "tf32": 1e-3, "bf16": 8e-3}
+MODES = ["split3", "tf32", "bf16"]
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _plan(m, q, mode):
+    from paper_1711_11224_gb300 import Plan
+    return Plan(m, [(v - 1) // 2 for v in q], mode=mode)
+
+
+SHAPES = [
+    ((3, 130, 40), (3, 5, 7)),        # two row tiles, ragged columns
+    ((4, 200, 148), (3, 7, 21)),      # 11 column tiles
+    ((2, 90, 33), (3, 31, 9)),        # 31 template rows
+    ((3, 20, 300), (1, 3, 5)),        # output rows wider than one CTA (two column groups)
+    ((50, 70), (7, 7)),               # n = 2
+    ((3, 4, 5), (7, 9, 11)),          # template larger than the volume
+]
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("m,q", SHAPES)
+def test_tc_forward_adjoint(mode, m, q):
+    X, H, R = synth.random_case(m, q, seed=3)
+    with _plan(m, q, mode) as pl:
+        pl.set_psf(_dev(H))
+        Y = pl.forward(_dev(X)).cpu().numpy()
+        G = pl.adjoint(_dev(R)).cpu().numpy()
+        pl.sync()
+    assert rel_l2(Y, oracle.forward(X, H)) <= TOL[mode]
+    assert rel_l2(G, oracle.adjoint(R, H)) <= TOL[mode]
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_tc_integer_exact(mode):
+    m, q = (4, 140, 60), (3, 5, 9)
+    X, H = synth.integer_case(m, q, seed=4)
+    rng = np.random.default_rng(1)
+    R = rng.integers(-4, 5, size=tuple(a + b - 1 for a, b in zip(m, q))).astype(np.float32)
+    with _plan(m, q, mode) as pl:
+        pl.set_psf(_dev(H))
+        Y = pl.forward(_dev(X)).cpu().numpy()
+        G = pl.adjoint(_dev(R)).cpu().numpy()
+    np.testing.assert_array_equal(Y.astype(np.float64), oracle.forward(X, H))
+    np.testing.assert_array_equal(G.astype(np.float64), oracle.adjoint(R, H))
+
+
+@pytest.mark.parametrize("mode", ["split3", "tf32"])
+def test_tc_iterate(mode):
+    """Steps 1-3 on the tensor cores: split-BF16x3 within the FP32 iteration bar after 20 steps."""
+    from paper_1711_11224_gb300 import Plan
+    P = synth.scaled_fil3d((24, 140, 50), (7, 9, 11), K=20)
+    with Plan(P.m, P.p, mode=mode) as pl:
+        pl.set_psf(_dev(P.H))
+        X, rep = pl.iterate(_dev(P.Y), K=20, x0="crop")
+        Xg = X.cpu().numpy()
+    ref = oracle.iterate(P.Y, P.H, oracle.x0_crop(P.Y, P.p), 20)
+    assert rep["accepted"] == 20 and rep["status"] == "CDV_OK"
+    assert np.all(np.diff(rep["f"]) < 0)
+    tol = TOL_ITER if mode == "split3" else 5e-3
+    assert rel_l2(Xg, ref["X"]) <= tol
+    # f = 1/2 ||Ax - y||^2: the residual cancels, so its relative error exceeds the per-convolution one
+    np.testing.assert_allclose(rep["f"], ref["f"], rtol=1e-4 if mode == "split3" else 2e-3)
+
+
+def test_tc_graph_matches_stream():
+    from paper_1711_11224_gb300 import Plan
+    P = synth.scaled_fil3d((10, 140, 40), (5, 5, 7), K=6)
+    outs = []
+    for g in (True, False):
+        with Plan(P.m, P.p, mode="split3") as pl:
+            pl.set_psf(_dev(P.H))
+            X, _ = pl.iterate(_dev(P.Y), K=6, x0="crop", use_graph=g)
+            outs.append(X.cpu().numpy())
+    np.testing.assert_array_equal(outs[0], outs[1])
+
+
+def test_tc_full_size_ring3d_sampled():
+    """512x512x128 with the 31x31x21 template in split-BF16x3, sampled outputs against the oracle."""
+    P = synth.ring3d()
+    rng = np.random.default_rng(0)
+    R = rng.standard_normal(P.Y.shape).astype(np.float32)
+    with _plan(P.m, P.H.shape, "split3") as pl:
+        pl.set_psf(_dev(P.H))
+        Y = pl.forward(_dev(P.X_true)).cpu().numpy()
+        G = pl.adjoint(_dev(R)).cpu().numpy()
+    rng = np.random.default_rng(1)
+    si = np.stack([rng.integers(0, s, 1500) for s in Y.shape], axis=1)
+    ki = np.stack([rng.integers(0, s, 1500) for s in G.shape], axis=1)
+    assert rel_l2(Y[tuple(si.T)], oracle.forward_points(P.X_true, P.H, si)) <= TOL_CONV
+    assert rel_l2(G[tuple(ki.T)], oracle.adjoint_points(R, P.H, ki)) <= TOL_CONV
+
+
+def test_tc_rl_is_fp32_only():
+    from paper_1711_11224_gb300 import CdvError
+    with _plan((4, 20, 20), (3, 3, 3), "bf16") as pl:
+        pl.set_psf(_dev(np.ones((3, 3, 3)) / 27))
+        with pytest.raises(CdvError, match="UNSUPPORTED"):
+            pl.richardson_lucy(_dev(np.ones((6, 22, 22))), _dev(np.ones((4, 20, 20))), 2)
