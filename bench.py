@@ -37,6 +37,34 @@ FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.55
 
+def measured_peaks():
+    """Measured BF16 dense peak of this machine's GPUs (TFLOP/s), else the recipe's fallback."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def roofline_peak(mode):
+    """(bound, peak TFLOP/s, basis) for the convolution kernels of a form."""
+    if mode == "fp32":
+        return "alu", FP32_PEAK_TFLOPS, "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (FFMA)"
+    bf16, src = measured_peaks()
+    if mode == "tf32":
+        return "tensor", bf16 * 1.1 / 2.25, "TF32 dense = %s BF16 peak %.1f x nominal ratio 1.1/2.25" % (src, bf16)
+    return "tensor", bf16, "%s BF16 dense peak (cuBLAS burst)" % src
+
+
+# executed tensor-pipe work per algorithmic multiply-add of the tensor-core forms: the Toeplitz
+# window (K of 48 for a 21-wide template) and, for split-BF16x3, three products
+def tc_executed_ratio(mode, q3):
+    ept = 4 if mode == "tf32" else 8
+    e = (ept - (q3 - 1) % ept) % ept
+    K = (e + q3 + 15 + 15) // 16 * 16
+    return (K / q3) * (3 if mode == "split3" else 1)
+
+
 WORKLOADS = {
     "ring3d": "X 512x512x128 filaments (320), H 31x31x21 Gaussian-plus-ring, Y = X (*) H + Poisson noise",
     "fil3d": "X 256x256x64 filaments (40) + background 10, H 15x15x11 Gaussian sigma (1.5,1.5,3), Poisson noise",
@@ -52,7 +80,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cdv", choices=["cdv", "reference"])
     ap.add_argument("--workload", default="ring3d", choices=sorted(WORKLOADS))
-    ap.add_argument("--mode", default="fp32", choices=["fp32", "bf16", "tf32", "split3"])
+    ap.add_argument("--mode", default="split3", choices=["fp32", "bf16", "tf32", "split3"],
+                    help="arithmetic of the convolutions (default: split-BF16x3, the fastest form within the FP32 "
+                         "accuracy bar)")
+    ap.add_argument("--no-forms", action="store_true", help="skip the per-form kernel timings and errors")
     ap.add_argument("--path", default="auto", choices=["auto", "general", "small"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -158,23 +189,62 @@ class Clocks:
 
 
 # ---------------------------------------------------------------- GPU arm
-def kernel_hash():
+def kernel_hash(mode):
     h = hashlib.sha256()
-    for f in ("conv_fp32.cuh",):
+    for f in (("conv_fp32.cuh",) if mode == "fp32" else ("conv_tc.cu",)):
         h.update(open(os.path.join(ROOT, "paper_1711_11224_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def traffic_record(workload, kernel):
+def traffic_record(workload, mode, kernel):
+    """DRAM bytes per launch from a committed ncu capture, or None if the kernel changed since."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path))
-        e = rec[workload][kernel]
-        if e.get("source_hash") != kernel_hash():
+        e = rec[workload][mode][kernel]
+        if e.get("source_hash") != kernel_hash(mode):
             return None
         return float(e["bytes_per_launch"])
     except Exception:
         return None
+
+
+def forms_report(P, dev, stream, npts=1000):
+    """Per form: kernel times of both convolutions and their relative L2 error on sampled outputs
+    against the FP64 oracle (same inputs: X_true for the forward, a seeded residual for the adjoint)."""
+    import torch
+
+    import oracle
+    from paper_1711_11224_gb300 import Plan
+    rng = np.random.default_rng(0)
+    Rn = rng.standard_normal(P.Y.shape).astype(np.float32)
+    si = np.stack([rng.integers(0, s, npts) for s in P.Y.shape], axis=1)
+    ki = np.stack([rng.integers(0, s, npts) for s in P.m], axis=1)
+    yo = oracle.forward_points(P.X_true, P.H, si)
+    go = oracle.adjoint_points(Rn, P.H, ki)
+    X = torch.from_numpy(P.X_true).to(dev)
+    Rt = torch.from_numpy(Rn).to(dev)
+    Y = torch.empty(P.Y.shape, device=dev, dtype=torch.float32)
+    G = torch.empty(P.m, device=dev, dtype=torch.float32)
+    flops = 2.0 * float(np.prod(P.m)) * float(P.H.size)
+    res = {}
+    for mode in ("fp32", "split3", "tf32", "bf16"):
+        pl = Plan(P.m, P.p, mode=mode)
+        pl.set_psf(torch.from_numpy(P.H).to(dev))
+        tf = time_kernel(lambda: pl.forward(X, Y), stream, reps=2)
+        ta = time_kernel(lambda: pl.adjoint(Rt, G), stream, reps=2)
+        Yh = Y.cpu().numpy()
+        Gh = G.cpu().numpy()
+        ef = float(np.linalg.norm(Yh[tuple(si.T)] - yo) / np.linalg.norm(yo))
+        ea = float(np.linalg.norm(Gh[tuple(ki.T)] - go) / np.linalg.norm(go))
+        bound, peak, _ = roofline_peak(mode)
+        res[mode] = {"forward_ms": tf * 1e3, "adjoint_ms": ta * 1e3,
+                     "gmacs_per_conv_pair": flops / (tf + ta) / 1e9,
+                     "forward_frac": flops / tf / 1e12 / peak, "adjoint_frac": flops / ta / 1e12 / peak,
+                     "bound": bound, "rel_l2_forward": ef, "rel_l2_adjoint": ea,
+                     "sample": "%d sampled outputs per operator vs the FP64 oracle" % npts}
+        pl.close()
+    return res
 
 
 def time_kernel(fn, stream, reps=3):
@@ -268,11 +338,14 @@ def run_cdv(args):
     gmac_rank = rep["gmac"]
     value = gmac_rank * ws / t
     iters = rep["accepted"] * ws / t
-    launches = 1 + 1 + 1 + 1 + 3 * (K + 16) + 1   # x0, state, initial forward, initial decide, slots, finalize
+    # x0, [x0 shadow], state, initial forward, initial decide, 3 per trial slot, finalize
+    launches = 1 + (0 if args.mode == "fp32" else 1) + 1 + 1 + 1 + 3 * (K + 16) + 1
 
+    dtype = {"fp32": "f32", "split3": "bf16x3 (split FP32, FP32 accumulate)", "tf32": "tf32 (FP32 accumulate)",
+             "bf16": "bf16 (FP32 accumulate)"}[args.mode]
     out = {"metric": METRIC, "value": value, "unit": "GMAC/s", "n_gpus": ws, "steps": K, "warmup": args.warmup,
            "ms_per_step": t * 1e3 / max(1, rep["accepted"]), "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32" if args.mode == "fp32" else args.mode, "data": "synthetic",
+           "vs_baseline": None, "dtype": dtype, "data": "synthetic",
            "config": {"workload": "%s: %s" % (args.workload, WORKLOADS[args.workload]), "mode": args.mode,
                       "path": args.path,
                       "K_per_call": K, "accepted": rep["accepted"], "rejected": rep["rejected"],
@@ -290,14 +363,23 @@ def run_cdv(args):
     flops = 2.0 * nxnh
     dom, tdom = ("forward", tf) if tf >= ta else ("adjoint", ta)
     achieved = flops / tdom / 1e12
-    traffic = traffic_record(args.workload, dom)
-    out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                       "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic, "kernel": "conv_fp32 " + dom,
+    bound, peak, basis = roofline_peak(args.mode)
+    kname = ("conv_fp32 " if args.mode == "fp32" else "conv_tc<%s> " % args.mode) + dom
+    traffic = traffic_record(args.workload, args.mode, dom)
+    out["roofline"] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                       "frac": achieved / peak, "traffic": traffic, "kernel": kname,
                        "forward_ms": tf * 1e3, "adjoint_ms": ta * 1e3,
-                       "forward_frac": flops / tf / 1e12 / FP32_PEAK_TFLOPS,
-                       "adjoint_frac": flops / ta / 1e12 / FP32_PEAK_TFLOPS,
-                       "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (FFMA)"}
+                       "forward_frac": flops / tf / 1e12 / peak, "adjoint_frac": flops / ta / 1e12 / peak,
+                       "peak_basis": basis,
+                       "achieved_is": "algorithmic flop (2 x prod(m) x prod(2p+1)) / kernel time"}
+    if args.mode != "fp32":
+        ratio = tc_executed_ratio(args.mode, P.H.shape[-1])
+        out["roofline"]["executed_tflops"] = achieved * ratio
+        out["roofline"]["executed_frac"] = achieved * ratio / peak
+        out["roofline"]["executed_per_algorithmic"] = ratio
     out["clocks"] = clk.summary()
+    if rank == 0 and not args.no_forms:
+        out["forms"] = forms_report(P, dev, stream)
 
     # end to end through the host-array C-ABI call (pinned buffers, copies inside the clock)
     if not args.no_e2e:
