@@ -215,6 +215,41 @@ cdv_status cdv_iterate_host(cdv_plan* plan, const float* Y_host, float* X_host, 
  */
 cdv_status cdv_richardson_lucy(cdv_plan* plan, const float* Y, float* X, int K, void* stream);
 
+/*
+ * Batched solver: `count` independent problems, volume i with n axes of
+ * m[i*n + a] samples and template half-widths p[i*n + a], all iterated
+ * together (Steps 1-3 per volume, each with its own step rule).  One trial
+ * slot runs batched launches whose work lists hold the tiles of every volume
+ * (one launch per template width along the contiguous axis), and the whole
+ * K-step run is replayed as one CUDA graph.  With autotune != 0 the tile shape
+ * of each volume and direction is chosen by timing the candidates at plan
+ * creation (results cached per process); iterates do not depend on the tile
+ * shape and equal those of cdv_iterate on each volume alone.  CDV_MODE_FP32
+ * only.  Allocates every workspace at creation; synchronises `stream`.
+ */
+typedef struct cdv_batch cdv_batch;
+cdv_status cdv_batch_plan_create(cdv_batch** out, int count, int n, const int64_t* m, const int32_t* p,
+                                 cdv_mode mode, int autotune, void* stream);
+
+/* Bytes of device memory the batch plan holds. */
+cdv_status cdv_batch_workspace_size(const cdv_batch* b, size_t* bytes);
+
+/* Templates of every volume: H[i] is a device pointer to prod(2p_i+1) floats (copied). */
+cdv_status cdv_batch_set_psfs(cdv_batch* b, const float* const* H, void* stream);
+
+/*
+ * K accepted steps for every volume (K <= 4096): Y[i] (device, m_i + 2p_i) and
+ * X[i] (device, m_i; x_0 per policy in, x_K out).  `reports`, if not NULL,
+ * points to `count` reports (their f_hist/delta_hist arrays optional) and the
+ * call then synchronises `stream`.  The captured graph is reused while the
+ * arrays, K and the options stay the same.
+ */
+cdv_status cdv_batch_iterate(cdv_batch* b, const float* const* Y, float* const* X, int K, const cdv_iter_opts* opts,
+                             cdv_iter_report* reports, void* stream);
+
+/* Free everything the batch plan owns.  NULL is accepted. */
+cdv_status cdv_batch_destroy(cdv_batch* b);
+
 /* Wait for `stream`, then return and clear the plan's device status word. */
 cdv_status cdv_plan_sync_status(cdv_plan* plan, void* stream);
 

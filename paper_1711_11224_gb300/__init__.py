@@ -8,9 +8,9 @@ All arithmetic runs in libcdv.so (hand-written CUDA, C ABI in include/cdv.h);
 this package marshals torch tensors into it.
 """
 from ._binding import CdvError, load  # noqa: F401
-from .plan import Plan  # noqa: F401
+from .plan import BatchPlan, Plan  # noqa: F401
 
-__all__ = ["Plan", "CdvError", "load", "conv", "ConvFn"]
+__all__ = ["Plan", "BatchPlan", "CdvError", "load", "conv", "ConvFn"]
 
 
 def __getattr__(name):

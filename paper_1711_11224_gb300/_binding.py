@@ -28,7 +28,8 @@ EXPORTS = [
     "cdv_status_string", "cdv_last_error", "cdv_version", "cdv_plan_create", "cdv_plan_workspace_size",
     "cdv_plan_set_psf", "cdv_plan_lipschitz", "cdv_plan_destroy", "cdv_forward", "cdv_adjoint", "cdv_grad_psf",
     "cdv_iter_opts_default", "cdv_iterate", "cdv_iterate_host", "cdv_richardson_lucy", "cdv_plan_sync_status",
-    "cdv_grad_psf_static",
+    "cdv_grad_psf_static", "cdv_batch_plan_create", "cdv_batch_workspace_size", "cdv_batch_set_psfs",
+    "cdv_batch_iterate", "cdv_batch_destroy",
 ]
 
 
@@ -85,6 +86,13 @@ def load(path=LIB_PATH):
     lib.cdv_richardson_lucy.argtypes = [vp, vp, vp, i32, vp]
     lib.cdv_plan_sync_status.argtypes = [vp, vp]
     lib.cdv_grad_psf_static.argtypes = [i32, i64p, ctypes.POINTER(ctypes.c_int32), i32, vp, vp, vp, vp]
+    lib.cdv_batch_plan_create.argtypes = [ctypes.POINTER(vp), i32, i32, i64p, ctypes.POINTER(ctypes.c_int32), i32, i32,
+                                          vp]
+    lib.cdv_batch_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    lib.cdv_batch_set_psfs.argtypes = [vp, ctypes.POINTER(vp), vp]
+    lib.cdv_batch_iterate.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i32, ctypes.POINTER(IterOpts),
+                                      ctypes.POINTER(IterReport), vp]
+    lib.cdv_batch_destroy.argtypes = [vp]
     _lib = lib
     return lib
 

@@ -75,6 +75,13 @@ struct ConvTile {
     size_t smem;         // dynamic shared memory bytes
 };
 
+// One volume of a batched launch of the FP32 engine.
+struct ConvBatchVol {
+    ConvLaunch L;
+    int ntx, nty, tiles2, tiles3;
+    size_t smem;
+};
+
 // FP32 direct-convolution engine (CUDA cores).
 bool conv_fp32_supported(int q3);
 ConvTile conv_fp32_tile(const ConvGeom& g);
@@ -85,6 +92,14 @@ cudaError_t grad_psf_prepare();
 // Per-Q3 launchers (one translation unit per group of template widths).
 template <int Q3>
 cudaError_t conv_fp32_launch_q(const ConvLaunch& L, const ConvTile& t, cudaStream_t s);
+template <int Q3>
+cudaError_t conv_fp32_batch_launch_q(const ConvBatchVol* vols, const int2* items, int nitems, size_t smem,
+                                     cudaStream_t s);
+// Batched launch over a work list (volume, tile) of volumes sharing template width q3; nitems == 0
+// prepares the kernel (outside stream capture).
+cudaError_t conv_fp32_batch_launch(int q3, const ConvBatchVol* vols, const int2* items, int nitems, size_t smem,
+                                   cudaStream_t s);
+ConvTile conv_fp32_tile_shape(const ConvGeom& g, int nty);
 
 // Iteration kernels (iterate.cu).
 cudaError_t launch_x0(int policy, float* x, const float* y, int64_t m1, int64_t m2, int64_t m3,
@@ -93,6 +108,20 @@ cudaError_t launch_state_init(IterState* st, double delta0, const double* absum,
                               int max_rejects, int K, int hist_cap, cudaStream_t s);
 cudaError_t launch_decide(const IterCtx& c, int nparts_f, int nparts_m, int init, cudaStream_t s);
 cudaError_t launch_finalize(const IterCtx& c, int64_t nx, cudaStream_t s);
+
+// Batched iteration: per-volume context read by the batched kernels.
+struct BatchVolCtx {
+    IterCtx c;
+    int64_t m1, m2, m3;
+    int p1, p2, p3;
+    int nparts_f, nparts_m;
+    const double* absum;
+};
+cudaError_t launch_batch_x0(const BatchVolCtx* v, int count, int policy, cudaStream_t s);
+cudaError_t launch_batch_state_init(const BatchVolCtx* v, int count, double delta0, double beta, int max_halvings,
+                                    int max_rejects, int K, int hist_cap, cudaStream_t s);
+cudaError_t launch_batch_decide(const BatchVolCtx* v, int count, int init, cudaStream_t s);
+cudaError_t launch_batch_finalize(const BatchVolCtx* v, int count, cudaStream_t s);
 
 // Template preparation (psf.cu).
 cudaError_t launch_flip(const float* h, float* ht, int q1, int q2, int q3, cudaStream_t s);

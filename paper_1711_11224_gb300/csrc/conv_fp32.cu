@@ -30,6 +30,33 @@ ConvTile conv_fp32_tile(const ConvGeom& g)
     return t;
 }
 
+cudaError_t conv_fp32_batch_launch(int q3, const ConvBatchVol* vols, const int2* items, int nitems, size_t smem,
+                                   cudaStream_t s)
+{
+    switch (q3) {
+#define CDV_CASE(Q) \
+    case Q: return conv_fp32_batch_launch_q<Q>(vols, items, nitems, smem, s);
+        CDV_CASE(1) CDV_CASE(3) CDV_CASE(5) CDV_CASE(7) CDV_CASE(9) CDV_CASE(11) CDV_CASE(13) CDV_CASE(15)
+        CDV_CASE(17) CDV_CASE(19) CDV_CASE(21) CDV_CASE(23) CDV_CASE(25) CDV_CASE(27) CDV_CASE(29) CDV_CASE(31)
+#undef CDV_CASE
+    default:
+        return cudaErrorInvalidValue;
+    }
+}
+
+// Tile of the FP32 engine with a given number of thread rows (nty <= 0: the default choice).
+ConvTile conv_fp32_tile_shape(const ConvGeom& g, int nty)
+{
+    ConvTile t = conv_fp32_tile(g);
+    if (nty <= 0) return t;
+    nty = (int)std::min<int64_t>(std::max(1, std::min(nty, kMaxThreads / t.ntx)), g.b2);
+    t.nty = nty;
+    t.tiles2 = (int)((g.b2 + nty - 1) / nty);
+    t.grid = t.tiles1 * t.tiles2 * t.tiles3;
+    t.smem = ConvSmem::make(t.ntx, t.nty, g.q2, g.q3).bytes();
+    return t;
+}
+
 cudaError_t conv_fp32_prepare(int q3)
 {
     ConvLaunch L{};

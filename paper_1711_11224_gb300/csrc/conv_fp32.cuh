@@ -94,14 +94,14 @@ struct ConvSmem {
 
 __device__ __forceinline__ int ring_slot(int64_t j1) { return (int)(((j1 % (kT1 + 1)) + (kT1 + 1)) % (kT1 + 1)); }
 
+// One CTA's output tile `tile` of volume `bidx` (batched plain calls) of the launch L.
 template <int Q3>
-__global__ void __launch_bounds__(kMaxThreads, 2)
-conv_fp32_kernel(const ConvLaunch L, const int ntx, const int nty, const int tiles2, const int tiles3)
+__device__ __forceinline__ void conv_fp32_body(const ConvLaunch& L, const int ntx, const int nty, const int tiles2,
+                                               const int tiles3, const int tile, const int bidx, float* smem)
 {
     constexpr int R3 = kR3, T1 = kT1;
     constexpr int WLP = ceil4(R3 + Q3 - 1);
     constexpr int Q3P = ceil4(Q3);
-    extern __shared__ __align__(16) float smem[];
 
     const ConvGeom& G = L.g;
     // The block has whole warps (blockDim.x = nthr rounded up to 32); threads
@@ -118,14 +118,12 @@ conv_fp32_kernel(const ConvLaunch L, const int ntx, const int nty, const int til
     float* s_tot = s_w + lay.tile_w;
     double* s_red = reinterpret_cast<double*>(smem + lay.floats());
 
-    int bt = blockIdx.x;
+    int bt = tile;
     const int t3 = bt % tiles3;
     bt /= tiles3;
     const int t2 = bt % tiles2;
     const int t1 = bt / tiles2;
     const int64_t S1 = (int64_t)t1 * T1, S2 = (int64_t)t2 * nty, S3 = (int64_t)t3 * ntx * R3;
-    const int bidx = blockIdx.y;
-
     const float* in = L.in ? L.in + bidx * L.in_bstride : nullptr;
     float* out = L.out ? L.out + bidx * L.out_bstride : nullptr;
     const int role = L.role;
@@ -317,9 +315,37 @@ conv_fp32_kernel(const ConvLaunch L, const int ntx, const int nty, const int til
         const double t = block_sum_f64((double)loc, s_red);
         if (tid == 0) {
             double* part = (role == ROLE_ADJ_TRIAL) ? L.ctx.part_m : L.ctx.part_f;
-            part[blockIdx.y * gridDim.x + blockIdx.x] = t;
+            part[tile] = t;
         }
     }
+}
+
+template <int Q3>
+__global__ void __launch_bounds__(kMaxThreads, 2)
+conv_fp32_kernel(const ConvLaunch L, const int ntx, const int nty, const int tiles2, const int tiles3)
+{
+    extern __shared__ __align__(16) float smem[];
+    conv_fp32_body<Q3>(L, ntx, nty, tiles2, tiles3, blockIdx.x, blockIdx.y, smem);
+}
+
+// Batched form: CTA i computes tile items[i].y of volume items[i].x, each volume with its own
+// geometry, buffers and tile shape (all volumes of one launch share the template width Q3).
+template <int Q3>
+__global__ void __launch_bounds__(kMaxThreads, 2) conv_fp32_batch_kernel(const ConvBatchVol* vols, const int2* items)
+{
+    extern __shared__ __align__(16) float smem[];
+    const int2 it = items[blockIdx.x];
+    const ConvBatchVol& V = vols[it.x];
+    conv_fp32_body<Q3>(V.L, V.ntx, V.nty, V.tiles2, V.tiles3, it.y, 0, smem);
+}
+
+template <int Q3>
+cudaError_t conv_fp32_batch_launch_q(const ConvBatchVol* vols, const int2* items, int nitems, size_t smem, cudaStream_t s)
+{
+    if (nitems <= 0)
+        return cudaFuncSetAttribute(conv_fp32_batch_kernel<Q3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    conv_fp32_batch_kernel<Q3><<<nitems, kMaxThreads, smem, s>>>(vols, items);
+    return cudaGetLastError();
 }
 
 template <int Q3>
@@ -334,9 +360,11 @@ cudaError_t conv_fp32_launch_q(const ConvLaunch& L, const ConvTile& t, cudaStrea
     return cudaGetLastError();
 }
 
-#define CDV_INSTANTIATE_FP32(Q) \
-    template cudaError_t conv_fp32_launch_q<Q>(const ConvLaunch&, const ConvTile&, cudaStream_t);
-#define CDV_EXTERN_FP32(Q) \
-    extern template cudaError_t conv_fp32_launch_q<Q>(const ConvLaunch&, const ConvTile&, cudaStream_t);
+#define CDV_INSTANTIATE_FP32(Q)                                                                       \
+    template cudaError_t conv_fp32_launch_q<Q>(const ConvLaunch&, const ConvTile&, cudaStream_t);       \
+    template cudaError_t conv_fp32_batch_launch_q<Q>(const ConvBatchVol*, const int2*, int, size_t, cudaStream_t);
+#define CDV_EXTERN_FP32(Q)                                                                            \
+    extern template cudaError_t conv_fp32_launch_q<Q>(const ConvLaunch&, const ConvTile&, cudaStream_t); \
+    extern template cudaError_t conv_fp32_batch_launch_q<Q>(const ConvBatchVol*, const int2*, int, size_t, cudaStream_t);
 
 }  // namespace cdv

@@ -45,8 +45,8 @@ cudaError_t launch_x0(int policy, float* x, const float* y, int64_t m1, int64_t 
     return cudaGetLastError();
 }
 
-__global__ void state_init_kernel(IterState* st, double delta0, const double* absum, double beta, int max_halvings,
-                                  int max_rejects, int K, int hist_cap)
+__device__ void state_init_kernel_body(IterState* st, double delta0, const double* absum, double beta,
+                                       int max_halvings, int max_rejects, int K, int hist_cap)
 {
     if (!(delta0 > 0.0)) {                // default step 1/L, L = (sum |h|)^2 >= ||A||_2^2
         const double a = *absum;
@@ -74,6 +74,12 @@ __global__ void state_init_kernel(IterState* st, double delta0, const double* ab
     st->pad_ = 0;
 }
 
+__global__ void state_init_kernel(IterState* st, double delta0, const double* absum, double beta, int max_halvings,
+                                  int max_rejects, int K, int hist_cap)
+{
+    state_init_kernel_body(st, delta0, absum, beta, max_halvings, max_rejects, K, hist_cap);
+}
+
 cudaError_t launch_state_init(IterState* st, double delta0, const double* absum, double beta, int max_halvings,
                               int max_rejects, int K, int hist_cap, cudaStream_t s)
 {
@@ -98,9 +104,8 @@ __device__ double block_reduce_fixed(const double* a, int n, double* sh)
     return t;
 }
 
-__global__ void __launch_bounds__(512) decide_kernel(IterCtx c, int nf, int nm, int init)
+__device__ void decide_body(const IterCtx& c, int nf, int nm, int init, double* sh)
 {
-    __shared__ double sh[512];
     IterState* st = c.st;
     if (st->done) return;
     const double F = 0.5 * block_reduce_fixed(c.part_f, nf, sh);
@@ -158,6 +163,12 @@ __global__ void __launch_bounds__(512) decide_kernel(IterCtx c, int nf, int nm, 
     }
 }
 
+__global__ void __launch_bounds__(512) decide_kernel(IterCtx c, int nf, int nm, int init)
+{
+    __shared__ double sh[512];
+    decide_body(c, nf, nm, init, sh);
+}
+
 cudaError_t launch_decide(const IterCtx& c, int nparts_f, int nparts_m, int init, cudaStream_t s)
 {
     decide_kernel<<<1, 512, 0, s>>>(c, nparts_f, nparts_m, init);
@@ -190,6 +201,77 @@ cudaError_t launch_fill(float* x, int64_t n, float v, cudaStream_t s)
 {
     const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
     fill_kernel<<<blocks, 256, 0, s>>>(x, n, v);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- batched forms (one volume per block row)
+
+__global__ void batch_x0_kernel(const BatchVolCtx* v, int policy)
+{
+    const BatchVolCtx& b = v[blockIdx.y];
+    if (policy == CDV_X0_GIVEN) return;
+    const int64_t n = b.m1 * b.m2 * b.m3;
+    const int64_t n2 = b.m2 + 2 * b.p2, n3 = b.m3 + 2 * b.p3;
+    float* x = b.c.x[0];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (policy == CDV_X0_ZERO) {
+            x[i] = 0.f;
+        } else {
+            const int64_t k3 = i % b.m3, k2 = (i / b.m3) % b.m2, k1 = i / (b.m2 * b.m3);
+            const float y = b.c.y[((k1 + b.p1) * n2 + (k2 + b.p2)) * n3 + (k3 + b.p3)];
+            x[i] = y > 0.f ? y : 0.f;
+        }
+    }
+}
+
+__global__ void batch_state_init_kernel(const BatchVolCtx* v, int count, double delta0, double beta, int max_halvings,
+                                        int max_rejects, int K, int hist_cap)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    state_init_kernel_body(v[i].c.st, delta0, v[i].absum, beta, max_halvings, max_rejects, K, hist_cap);
+}
+
+__global__ void __launch_bounds__(512) batch_decide_kernel(const BatchVolCtx* v, int init)
+{
+    __shared__ double sh[512];
+    const BatchVolCtx& b = v[blockIdx.x];
+    decide_body(b.c, b.nparts_f, b.nparts_m, init, sh);
+}
+
+__global__ void batch_finalize_kernel(const BatchVolCtx* v)
+{
+    const BatchVolCtx& b = v[blockIdx.y];
+    if (b.c.st->cur == 0) return;
+    const int64_t n = b.m1 * b.m2 * b.m3;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b.c.x[0][i] = b.c.x[1][i];
+}
+
+cudaError_t launch_batch_x0(const BatchVolCtx* v, int count, int policy, cudaStream_t s)
+{
+    if (policy == CDV_X0_GIVEN) return cudaSuccess;
+    batch_x0_kernel<<<dim3(64, count), 256, 0, s>>>(v, policy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_state_init(const BatchVolCtx* v, int count, double delta0, double beta, int max_halvings,
+                                    int max_rejects, int K, int hist_cap, cudaStream_t s)
+{
+    batch_state_init_kernel<<<(count + 127) / 128, 128, 0, s>>>(v, count, delta0, beta, max_halvings, max_rejects, K,
+                                                                hist_cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_decide(const BatchVolCtx* v, int count, int init, cudaStream_t s)
+{
+    batch_decide_kernel<<<count, 512, 0, s>>>(v, init);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_finalize(const BatchVolCtx* v, int count, cudaStream_t s)
+{
+    batch_finalize_kernel<<<dim3(64, count), 256, 0, s>>>(v);
     return cudaGetLastError();
 }
 

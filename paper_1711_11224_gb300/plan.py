@@ -187,3 +187,86 @@ class Plan:
 
     def sync(self):
         B.check(self.lib.cdv_plan_sync_status(self._h, _stream()))
+
+
+class BatchPlan:
+    """Many independent problems iterated together (FP32): volume i has m[i] samples, half-widths p[i]."""
+
+    def __init__(self, ms, ps, autotune=True):
+        self.lib = B.load()
+        self.ms = [tuple(int(v) for v in m) for m in ms]
+        self.ps = [tuple(int(v) for v in p) for p in ps]
+        self.count = len(self.ms)
+        self.n = len(self.ms[0])
+        if self.count < 1 or len(self.ps) != self.count or any(len(m) != self.n or len(p) != self.n
+                                                               for m, p in zip(self.ms, self.ps)):
+            raise ValueError("one (m, p) pair of the same n per volume")
+        self.qs = [tuple(2 * v + 1 for v in p) for p in self.ps]
+        self.ny_shapes = [tuple(a + 2 * b for a, b in zip(m, p)) for m, p in zip(self.ms, self.ps)]
+        mm = (ctypes.c_int64 * (self.count * self.n))(*[v for m in self.ms for v in m])
+        pp = (ctypes.c_int32 * (self.count * self.n))(*[v for p in self.ps for v in p])
+        h = ctypes.c_void_p()
+        B.check(self.lib.cdv_batch_plan_create(ctypes.byref(h), self.count, self.n, mm, pp, 0,
+                                               1 if autotune else 0, _stream()))
+        self._h = h
+        self.H = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.cdv_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def workspace_bytes(self):
+        v = ctypes.c_size_t()
+        B.check(self.lib.cdv_batch_workspace_size(self._h, ctypes.byref(v)))
+        return int(v.value)
+
+    def _ptrs(self, ts):
+        return (ctypes.c_void_p * self.count)(*[t.data_ptr() for t in ts])
+
+    def set_psfs(self, Hs):
+        for H, q in zip(Hs, self.qs):
+            _need(H, q, "H")
+        B.check(self.lib.cdv_batch_set_psfs(self._h, self._ptrs(Hs), _stream()))
+        self.H = list(Hs)
+        return self
+
+    def iterate(self, Ys, Xs=None, K=100, report=True, **kw):
+        """K accepted steps of Steps 1-3 for every volume; returns (Xs, reports)."""
+        for Y, s in zip(Ys, self.ny_shapes):
+            _need(Y, s, "Y")
+        if Xs is None:
+            Xs = [torch.empty(m, device=Ys[0].device, dtype=torch.float32) for m in self.ms]
+            kw.setdefault("x0", "crop")
+        for X, m in zip(Xs, self.ms):
+            _need(X, m, "X")
+        kw.pop("path", None)
+        o = Plan.opts(**kw)
+        reps = None
+        hist = []
+        if report:
+            reps = (B.IterReport * self.count)()
+            for r in reps:
+                f = np.zeros(K + 1)
+                d = np.zeros(max(K, 1))
+                r.f_hist = f.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+                r.delta_hist = d.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+                hist.append((f, d))
+        B.check(self.lib.cdv_batch_iterate(self._h, self._ptrs(Ys), self._ptrs(Xs), int(K), ctypes.byref(o),
+                                           reps, _stream()))
+        if not report:
+            return Xs, None
+        return Xs, [Plan._pack(r, f, d) for r, (f, d) in zip(reps, hist)]

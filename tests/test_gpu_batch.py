@@ -1,0 +1,95 @@
+"""Batched solver: many uneven volumes with their own templates iterated together.
+
+A volume's iterates do not depend on the tile shape nor on the other volumes,
+so the batched result must equal cdv_iterate on each volume alone, bit for
+bit; cdv_iterate itself is held to the FP64 oracle elsewhere, and here too
+on two small volumes.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from _util import TOL_ITER, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SHAPES = [((12, 30, 40), (5, 5, 7)), ((8, 50, 33), (3, 7, 9)), ((20, 20, 20), (7, 3, 5)),
+          ((6, 64, 17), (3, 5, 7)), ((16, 16, 64), (1, 3, 11))]
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _problems(shapes, K):
+    return [synth.scaled_fil3d(m, q, seed=i, K=K) for i, (m, q) in enumerate(shapes)]
+
+
+def _single(P, K, **kw):
+    from paper_1711_11224_gb300 import Plan
+    with Plan(P.m, P.p) as pl:
+        pl.set_psf(_dev(P.H))
+        X, rep = pl.iterate(_dev(P.Y), K=K, x0="crop", path="general", **kw)
+        return X.cpu().numpy(), rep
+
+
+@pytest.mark.parametrize("autotune", [True, False])
+def test_batch_equals_single_volume_runs(autotune):
+    from paper_1711_11224_gb300 import BatchPlan
+    K = 8
+    probs = _problems(SHAPES, K)
+    with BatchPlan([P.m for P in probs], [P.p for P in probs], autotune=autotune) as bp:
+        bp.set_psfs([_dev(P.H) for P in probs])
+        Xs, reps = bp.iterate([_dev(P.Y) for P in probs], K=K, x0="crop")
+        Xb = [X.cpu().numpy() for X in Xs]
+    for P, X, r in zip(probs, Xb, reps):
+        Xs_, rs = _single(P, K)
+        assert r["accepted"] == rs["accepted"] == K and r["status"] == "CDV_OK"
+        np.testing.assert_array_equal(X, Xs_)
+        np.testing.assert_allclose(r["f"], rs["f"], rtol=1e-12)
+
+
+def test_batch_matches_oracle():
+    from paper_1711_11224_gb300 import BatchPlan
+    probs = _problems(SHAPES[:2], 10)
+    with BatchPlan([P.m for P in probs], [P.p for P in probs]) as bp:
+        bp.set_psfs([_dev(P.H) for P in probs])
+        Xs, reps = bp.iterate([_dev(P.Y) for P in probs], K=10, x0="crop")
+    for P, X, r in zip(probs, Xs, reps):
+        ref = oracle.iterate(P.Y, P.H, oracle.x0_crop(P.Y, P.p), 10)
+        assert r["accepted"] == ref["accepted"] == 10
+        assert rel_l2(X.cpu().numpy(), ref["X"]) <= TOL_ITER
+        np.testing.assert_allclose(r["f"], ref["f"], rtol=1e-5)
+
+
+def test_batch_graph_replay_and_repeat():
+    from paper_1711_11224_gb300 import BatchPlan
+    probs = _problems(SHAPES[:3], 5)
+    with BatchPlan([P.m for P in probs], [P.p for P in probs]) as bp:
+        bp.set_psfs([_dev(P.H) for P in probs])
+        Ys = [_dev(P.Y) for P in probs]
+        Xs = [torch.empty(P.m, device="cuda") for P in probs]
+        outs = []
+        for g in (True, True, False):
+            bp.iterate(Ys, Xs, K=5, x0="crop", use_graph=g)
+            outs.append([X.cpu().numpy() for X in Xs])
+    for a, b in zip(outs[0], outs[1]):
+        np.testing.assert_array_equal(a, b)
+    for a, b in zip(outs[0], outs[2]):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_batch64_workload_subset_equals_single():
+    """64 uneven volumes (sizes U[32,256]^2 x U[16,128], templates odd U[5,21]), 200 steps, one graph."""
+    from paper_1711_11224_gb300 import BatchPlan
+    probs = synth.batch64(K=200)
+    with BatchPlan([P.m for P in probs], [P.p for P in probs]) as bp:
+        bp.set_psfs([_dev(P.H) for P in probs])
+        Xs, reps = bp.iterate([_dev(P.Y) for P in probs], K=200, x0="crop")
+    assert all(r["status"] == "CDV_OK" and r["accepted"] == 200 for r in reps)
+    assert all(np.all(np.diff(r["f"]) < 0) for r in reps)
+    for i in (0, 17, 40, 63):
+        Xs_, rs = _single(probs[i], 200)
+        np.testing.assert_array_equal(Xs[i].cpu().numpy(), Xs_)
