@@ -174,3 +174,18 @@ def test_small_path_rejects_large_problem():
         pl.set_psf(_dev(np.ones((3, 3, 3)) / 27))
         with pytest.raises(CdvError, match="UNSUPPORTED"):
             pl.iterate(_dev(np.zeros((66, 66, 66))), K=1, path="small")
+
+
+def test_resume_equals_uninterrupted_run():
+    """Checkpoint/resume: K1 steps, then K - K1 more from the saved iterate, equal K steps at once."""
+    from paper_1711_11224_gb300 import Plan
+    P = synth.scaled_fil3d((10, 40, 36), (5, 7, 9), K=12)
+    with Plan(P.m, P.p) as pl:
+        pl.set_psf(_dev(P.H))
+        Y = _dev(P.Y)
+        Xa, ra = pl.iterate(Y, K=12, x0="crop", path="general")
+        Xb, rb1 = pl.iterate(Y, K=5, x0="crop", path="general")
+        ckpt = Xb.cpu().numpy()                                   # the whole iteration state at a fixed step rule
+        Xc, rb2 = pl.iterate(Y, _dev(ckpt), K=7, x0="given", path="general")
+    np.testing.assert_array_equal(Xa.cpu().numpy(), Xc.cpu().numpy())
+    np.testing.assert_array_equal(ra["f"][5:], rb2["f"])
