@@ -154,8 +154,8 @@ static bool tc_config(const cdv_plan* P, const ConvGeom& g, bool fwd, TcArgs& t)
     t.e = ((off % ept) + ept) % ept;
     t.K = (t.e + g.q3 + 15 + 15) / 16 * 16;
     t.kchunks = t.K / ept;
-    t.P = 8;
-    t.MT = 2;
+    t.P = 16;
+    t.MT = 1;
     t.rows = (128 * t.MT + g.q2 - 1 + 15) / 16 * 16;
     t.tiles1 = ceil_div(g.b1, t.P);
     t.tiles2 = ceil_div(g.b2, 128 * t.MT);
@@ -163,7 +163,7 @@ static bool tc_config(const cdv_plan* P, const ConvGeom& g, bool fwd, TcArgs& t)
     const int64_t grid = (int64_t)t.tiles1 * t.tiles2 * t.tiles3;
     if (grid > (1LL << 31) - 1 || t.rows / 2 > 256 || t.K > 256) return false;
     t.grid = (int)grid;
-    t.tmem_cols = 512;
+    t.tmem_cols = 512;                      // 2 partial buffers x 16 planes x 16 columns
     t.sh_pitch = fwd ? P->pitch_r : P->pitch_x;
     t.err = P->dev_err;
     // deepest template-tile ring that fits: each stage is one template row of one input plane

@@ -13,10 +13,12 @@
 // Shapes chosen for the tensor pipe (an M128 x K16 MMA costs about
 // max(46, N/2) cycles, so N must be large):
 //  * N = 16 x (output planes): one input plane u and template row j2 feed the
-//    CTA's P = 8 output planes through Toeplitz tiles of consecutive j1, which
-//    are stored side by side ([j2][K chunk][j1*16 + n]), so one MMA with
-//    N = 16 x (planes in range) updates all of them.
-//  * M = 2 x 128 rows per CTA: both M tiles share each staged B stage.
+//    CTA's P = 16 output planes through Toeplitz tiles of consecutive j1,
+//    which are stored side by side ([j2][K chunk][j1*16 + n]), so one MMA
+//    with N = 16 x (planes in range) <= 256 updates all of them.
+//  * M = 128 rows per CTA.  Split-BF16x3 issues hi*hi and hi*lo back to back
+//    with the A operand kept in the tensor core's collector buffer, so A is
+//    read from shared memory twice per three products.
 //  * The row shift j2 is a 16-byte shift of the shared-memory descriptor of
 //    one TMA-staged tile of plane u (K-major, no swizzle: core matrices of
 //    8 rows x 16 bytes, rows 16 bytes apart), so the tile serves all q2 rows.
@@ -31,13 +33,14 @@
 //               two boxes of rows/2 rows, zero-filled outside the volume) and,
 //               per template row, the Toeplitz tiles of the planes in range
 //               (bulk copies through a 4-stage ring).
-//   warp 1      MMA issuer (one thread): per (j2, K step, M tile) one MMA,
-//               three for split-BF16x3 (hi*hi, hi*lo, lo*hi); tcgen05.commit
+//   warp 1      MMA issuer (one thread): per (j2, K step) one MMA, three
+//               for split-BF16x3 (hi*hi, hi*lo, lo*hi); tcgen05.commit
 //               releases ring stages and hands each plane's partial to the
 //               epilogue.
-//   warps 2-9   epilogue, one warpgroup per M tile, one output row per thread:
-//               drains the partials, then the fused epilogue of the FP32
-//               engine plus the BF16/TF32 shadows the next convolution reads.
+//   warps 2-9   epilogue, one output row per thread, each warpgroup owning 8 of
+//               the 16 columns: drains the partials, then the fused epilogue
+//               of the FP32 engine plus the BF16/TF32 shadows the next
+//               convolution reads.
 // Every wait is bounded (about 0.5 s).  A wait that runs out records
 // CDV_ERR_TIMEOUT in the device error word; the CTA stops issuing work, waits
 // for its own copies and MMAs, frees its TMEM and exits.  CTAs that start
@@ -56,8 +59,9 @@ namespace {
 
 constexpr int kM = 128;
 constexpr int kN = 16;
-constexpr int kP = 8;          // output planes per CTA
-constexpr int kMT = 2;         // M tiles per CTA
+constexpr int kP = 16;         // output planes per CTA (N of one MMA up to 256)
+constexpr int kMT = 1;         // M tiles per CTA
+constexpr int kEC = 8;         // accumulator columns per plane drained by one epilogue warpgroup
 constexpr int kThreads = 320;
 
 __device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -105,6 +109,21 @@ __device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned
                  "l"(src), "r"(bytes), "r"(bar)
                  : "memory");
 }
+// BF16 MMA that loads A into the collector buffer (fill) or reuses it and frees it (lastuse).
+__device__ __forceinline__ void mma_bf16_fill(unsigned d, uint64_t a, uint64_t b, unsigned idesc, unsigned acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, "
+        "%3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_bf16_lastuse(unsigned d, uint64_t a, uint64_t b, unsigned idesc, unsigned acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, "
+        "%2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
 template <int KIND>
 __device__ __forceinline__ void mma(unsigned d, uint64_t a, uint64_t b, unsigned idesc, unsigned acc)
 {
@@ -124,6 +143,16 @@ __device__ __forceinline__ void mbar_arrive(unsigned bar)
 __device__ __forceinline__ void mma_commit(unsigned bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tmem_ld8(unsigned taddr, float* v)
+{
+    unsigned r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; i++) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tmem_ld16(unsigned taddr, float* v)
 {
@@ -352,10 +381,13 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
                         const unsigned d = tmem + (unsigned)(((mt * 2 + b) * T.P + ilo) * kN);
                         const unsigned acc = (j2 == 0 && k == 0) ? 0u : 1u;   // fresh partial per input plane
                         const uint64_t ad_hi = sdesc(a_hi + aoff, lbo_a, 128);
-                        mma<KIND>(d, ad_hi, bd_hi, idesc, acc);
                         if (KIND == CDV_MODE_SPLIT_BF16X3) {
-                            mma<KIND>(d, ad_hi, bd_lo, idesc, 1u);
+                            // hi*hi and hi*lo share A: the second reuses it from the collector buffer
+                            mma_bf16_fill(d, ad_hi, bd_hi, idesc, acc);
+                            mma_bf16_lastuse(d, ad_hi, bd_lo, idesc, 1u);
                             mma<KIND>(d, sdesc(a_lo + aoff, lbo_a, 128), bd_hi, idesc, 1u);
+                        } else {
+                            mma<KIND>(d, ad_hi, bd_hi, idesc, acc);
                         }
                     }
                 }
@@ -371,19 +403,19 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
         if (!mbar_wait(DRAIN, 0)) fail();
     }
 
-    // ---------------- epilogue (warps 2..9): one M tile per warpgroup, one output row per thread
+    // ---------------- epilogue (warps 2..9): one output row per thread; warpgroup g drains and owns
+    // columns [8g, 8g + 8) of every plane's 16-column accumulator
     float loc = 0.f;
     if (warp >= 2) {
-        const int mt = (warp - 2) >> 2;
+        const int cg = (warp - 2) >> 2;
         const int quarter = warp & 3;
         const int m = quarter * 32 + lane;
-        const int64_t s2 = S2 + (int64_t)mt * kM + m;
-        const bool tile_ok = S2 + (int64_t)mt * kM < G.b2;
-        float tot[kP][kN];
+        const int64_t s2 = S2 + m;
+        float tot[kP][kEC];
 #pragma unroll
         for (int i = 0; i < kP; i++)
 #pragma unroll
-            for (int c = 0; c < kN; c++) tot[i][c] = 0.f;
+            for (int c = 0; c < kEC; c++) tot[i][c] = 0.f;
         bool ok = true;
         if (have_work) {
             int it = 0;
@@ -398,15 +430,13 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 int ilo, ihi;
                 plane_range(u, ilo, ihi);
-                if (tile_ok) {
 #pragma unroll
-                    for (int i = 0; i < kP; i++) {
-                        if (i < ilo || i > ihi) continue;                 // warp-uniform
-                        float v[kN];
-                        tmem_ld16(tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)(((mt * 2 + b) * T.P + i) * kN), v);
+                for (int i = 0; i < kP; i++) {
+                    if (i < ilo || i > ihi) continue;                 // warp-uniform
+                    float v[kEC];
+                    tmem_ld8(tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)((b * T.P + i) * kN + cg * kEC), v);
 #pragma unroll
-                        for (int c = 0; c < kN; c++) tot[i][c] += v[c];
-                    }
+                    for (int c = 0; c < kEC; c++) tot[i][c] += v[c];
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
                 __syncwarp();
@@ -414,14 +444,14 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
             }
         }
         if (!ok && lane == 0) fail();
-        if (ok && tile_ok && s2 < G.b2) {
+        if (ok && s2 < G.b2) {
 #pragma unroll
             for (int i = 0; i < kP; i++) {
                 const int64_t s1 = S1 + i;
                 if (s1 >= G.b1) continue;
 #pragma unroll
-                for (int c = 0; c < kN; c++) {
-                    const int64_t s3 = S3 + c;
+                for (int c = 0; c < kEC; c++) {
+                    const int64_t s3 = S3 + cg * kEC + c;
                     if (s3 >= G.b3) continue;
                     const int64_t idx = (s1 * G.b2 + s2) * G.b3 + s3;
                     const int64_t sidx = (s1 * G.b2 + s2) * T.sh_pitch + s3;
