@@ -355,7 +355,10 @@ def run_batch(args):
             seq += e0.elapsed_time(e1) / 1e3
     nconv = len(probs) * (1 + 2 * K)
     ng = len({P.H.shape[-1] for P in probs})          # one batched launch per template width per convolution
-    launches = 1 + 1 + ng + 1 + (K + 16) * (2 * ng + 1) + 1   # x0, state, forward, decide, slots, finalize
+    trials = max(r["trials"] for r in reps)
+    # x0, state, forward per width, decision, then per trial slot: adjoint and forward per width, decision,
+    # loop condition; finalize
+    launches = 1 + 1 + ng + 1 + trials * (2 * ng + 2) + 1
     out = {"metric": METRIC, "value": gmac / t, "unit": "GMAC/s", "n_gpus": ws, "steps": K,
            "warmup": args.warmup, "ms_per_step": t * 1e3 / max(1, acc), "higher_is_better": True,
            "scaling": "strong" if ws > 1 else "weak",
@@ -422,8 +425,9 @@ def run_cdv(args):
     gmac_rank = rep["gmac"]
     value = gmac_rank * ws / t
     iters = rep["accepted"] * ws / t
-    # x0, [x0 shadow], state, initial forward, initial decide, 3 per trial slot, finalize
-    launches = 1 + (0 if args.mode == "fp32" else 1) + 1 + 1 + 1 + 3 * (K + 16) + 1
+    # one graph: x0, [x0 shadow], state, initial forward, initial decision, then a WHILE loop of trial
+    # slots (adjoint, forward, decision: 3 launches per trial), finalize
+    launches = 1 + (0 if args.mode == "fp32" else 1) + 1 + 1 + 1 + 3 * rep["trials"] + 1
 
     dtype = {"fp32": "f32", "split3": "bf16x3 (split FP32, FP32 accumulate)", "tf32": "tf32 (FP32 accumulate)",
              "bf16": "bf16 (FP32 accumulate)"}[args.mode]

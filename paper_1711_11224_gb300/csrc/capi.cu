@@ -501,58 +501,95 @@ static IterCtx make_ctx(cdv_plan* P, const float* Y, float* X)
     return c;
 }
 
-static cdv_status enqueue_run_tc(cdv_plan* P, const float* Y, float* X, int K, const cdv_iter_opts& o, cudaStream_t s)
+// One projected-gradient run as three phases: 0 = prologue (x_0, state, initial forward and decision),
+// 1 = one trial slot (adjoint + update, forward + residual, decision), 2 = epilogue (x_K into X).
+struct RunCtx {
+    cdv_plan* P;
+    const float* Y;
+    float* X;
+    int K;
+    cdv_iter_opts o;
+};
+
+static cdv_status run_phase(void* vctx, int phase, bool loop, unsigned long long h, cudaStream_t s)
 {
-    const IterCtx c = make_ctx(P, Y, X);
-    CDV_CUDA(launch_x0(o.x0_policy, X, Y, P->m[0], P->m[1], P->m[2], P->p[0], P->p[1], P->p[2], s), "x0");
-    CDV_CUDA(tc_shadow(X, P->m[0] * P->m[1], P->m[2], P->pitch_x, (int)P->mode, P->xsh[0][0], P->xsh[0][1], s),
-             "x0 shadow");
-    CDV_CUDA(launch_state_init(P->st, o.delta0, P->absum, o.beta, o.max_halvings, o.max_rejects, K, kHistCap, s), "state");
-    TcArgs F = P->tcf, A = P->tca;
-    F.ctx = c;
-    A.ctx = c;
-    F.role = ROLE_FWD_INIT;
-    CDV_CUDA(tc_launch(F, P->map_x, s), "forward (initial, tensor cores)");
-    CDV_CUDA(launch_decide(c, F.grid, 0, 1, s), "decide (initial)");
-    F.role = ROLE_FWD_TRIAL;
-    A.role = ROLE_ADJ_TRIAL;
-    const int slots = K + o.max_rejects;
-    for (int i = 0; i < slots && K > 0; i++) {
-        CDV_CUDA(tc_launch(A, P->map_r, s), "adjoint trial (tensor cores)");
-        CDV_CUDA(tc_launch(F, P->map_x, s), "forward trial (tensor cores)");
-        CDV_CUDA(launch_decide(c, F.grid, A.grid, 0, s), "decide");
+    RunCtx& R = *static_cast<RunCtx*>(vctx);
+    cdv_plan* P = R.P;
+    const IterCtx c = make_ctx(P, R.Y, R.X);
+    const int max_trials = R.K + R.o.max_rejects + 1;
+    int nf, nm;
+    if (P->tc()) {
+        nf = P->tcf.grid;
+        nm = P->tca.grid;
+    } else {
+        nf = P->tf.grid;
+        nm = P->ta.grid;
     }
-    CDV_CUDA(launch_finalize(c, P->nx, s), "finalize");
+    auto decide = [&](int init) -> cudaError_t {
+        return loop ? launch_decide_loop(c, nf, init ? 0 : nm, init, h, max_trials, s)
+                    : launch_decide(c, nf, init ? 0 : nm, init, s);
+    };
+    if (phase == 0) {
+        CDV_CUDA(launch_x0(R.o.x0_policy, R.X, R.Y, P->m[0], P->m[1], P->m[2], P->p[0], P->p[1], P->p[2], s), "x0");
+        if (P->tc())
+            CDV_CUDA(tc_shadow(R.X, P->m[0] * P->m[1], P->m[2], P->pitch_x, (int)P->mode, P->xsh[0][0], P->xsh[0][1], s),
+                     "x0 shadow");
+        CDV_CUDA(launch_state_init(P->st, R.o.delta0, P->absum, R.o.beta, R.o.max_halvings, R.o.max_rejects, R.K,
+                                   kHistCap, s), "state");
+        if (P->tc()) {
+            TcArgs F = P->tcf;
+            F.ctx = c;
+            F.role = ROLE_FWD_INIT;
+            CDV_CUDA(tc_launch(F, P->map_x, s), "forward (initial, tensor cores)");
+        } else {
+            ConvLaunch F{};
+            F.g = P->gf;
+            F.w = P->H;
+            F.batch = 1;
+            F.ctx = c;
+            F.role = ROLE_FWD_INIT;
+            CDV_CUDA(conv_fp32_launch(F, P->tf, s), "forward (initial)");
+        }
+        CDV_CUDA(decide(1), "decide (initial)");
+    } else if (phase == 1) {
+        if (P->tc()) {
+            TcArgs F = P->tcf, A = P->tca;
+            F.ctx = c;
+            A.ctx = c;
+            F.role = ROLE_FWD_TRIAL;
+            A.role = ROLE_ADJ_TRIAL;
+            CDV_CUDA(tc_launch(A, P->map_r, s), "adjoint trial (tensor cores)");
+            CDV_CUDA(tc_launch(F, P->map_x, s), "forward trial (tensor cores)");
+        } else {
+            ConvLaunch F{};
+            F.g = P->gf;
+            F.w = P->H;
+            F.batch = 1;
+            F.ctx = c;
+            ConvLaunch A = F;
+            A.g = P->ga;
+            A.w = P->Ht;
+            F.role = ROLE_FWD_TRIAL;
+            A.role = ROLE_ADJ_TRIAL;
+            CDV_CUDA(conv_fp32_launch(A, P->ta, s), "adjoint trial");
+            CDV_CUDA(conv_fp32_launch(F, P->tf, s), "forward trial");
+        }
+        CDV_CUDA(decide(0), "decide");
+    } else {
+        CDV_CUDA(launch_finalize(c, P->nx, s), "finalize");
+    }
     return CDV_OK;
 }
 
+// Stream form: the prologue, K + max_rejects trial slots (slots after the run has finished return at
+// once) and the epilogue.
 static cdv_status enqueue_run(cdv_plan* P, const float* Y, float* X, int K, const cdv_iter_opts& o, cudaStream_t s)
 {
-    if (P->tc()) return enqueue_run_tc(P, Y, X, K, o, s);
-    const IterCtx c = make_ctx(P, Y, X);
-    CDV_CUDA(launch_x0(o.x0_policy, X, Y, P->m[0], P->m[1], P->m[2], P->p[0], P->p[1], P->p[2], s), "x0");
-    CDV_CUDA(launch_state_init(P->st, o.delta0, P->absum, o.beta, o.max_halvings, o.max_rejects, K, kHistCap, s), "state");
-    ConvLaunch F{};
-    F.g = P->gf;
-    F.w = P->H;
-    F.batch = 1;
-    F.ctx = c;
-    ConvLaunch A = F;
-    A.g = P->ga;
-    A.w = P->Ht;
-    F.role = ROLE_FWD_INIT;
-    CDV_CUDA(conv_fp32_launch(F, P->tf, s), "forward (initial)");
-    CDV_CUDA(launch_decide(c, P->tf.grid, 0, 1, s), "decide (initial)");
-    F.role = ROLE_FWD_TRIAL;
-    A.role = ROLE_ADJ_TRIAL;
-    const int slots = K + o.max_rejects;
-    for (int i = 0; i < slots && K > 0; i++) {
-        CDV_CUDA(conv_fp32_launch(A, P->ta, s), "adjoint trial");
-        CDV_CUDA(conv_fp32_launch(F, P->tf, s), "forward trial");
-        CDV_CUDA(launch_decide(c, P->tf.grid, P->ta.grid, 0, s), "decide");
-    }
-    CDV_CUDA(launch_finalize(c, P->nx, s), "finalize");
-    return CDV_OK;
+    RunCtx R{P, Y, X, K, o};
+    cdv_status st = run_phase(&R, 0, false, 0, s);
+    for (int i = 0; st == CDV_OK && K > 0 && i < K + o.max_rejects; i++) st = run_phase(&R, 1, false, 0, s);
+    if (st == CDV_OK) st = run_phase(&R, 2, false, 0, s);
+    return st;
 }
 
 static cdv_status fill_report(cdv_plan* P, int K, cdv_iter_report* rep, cudaStream_t s)
@@ -631,15 +668,12 @@ cdv_status cdv_iterate(cdv_plan* plan, const float* Y, float* X, int K, const cd
             plan->gexec = nullptr;
             plan->graph = nullptr;
             plan->key_valid = false;
-            CDV_CUDA(cudaStreamBeginCapture(plan->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
-            cdv_status st = enqueue_run(plan, Y, X, K, o, plan->cap);
+            // prologue -> WHILE(trial slot) -> epilogue: the device-side decision ends the loop, so no
+            // spare slots are launched
+            RunCtx R{plan, Y, X, K, o};
             cudaGraph_t gr = nullptr;
-            cudaError_t e = cudaStreamEndCapture(plan->cap, &gr);
-            if (st != CDV_OK) {
-                if (gr) cudaGraphDestroy(gr);
-                return st;
-            }
-            if (e != cudaSuccess) return cuda_fail(e, "end capture");
+            cdv_status st = build_loop_graph(plan->cap, run_phase, &R, &gr);
+            if (st != CDV_OK) return st;
             plan->graph = gr;
             CDV_CUDA(cudaGraphInstantiate(&plan->gexec, gr, 0), "instantiate graph");
             plan->key = k;

@@ -6,7 +6,8 @@
 // present (each CTA of such a launch computes one tile of one volume, chosen
 // from a work list ordered largest volume first), plus one batched decision
 // launch (one block per volume, each with its own FP64 step rule).  The whole
-// K-step run is captured once into a CUDA graph and replayed.  Per-volume tile
+// K-step run is one CUDA graph (a WHILE loop over trial slots that ends when
+// every volume is done), captured once and replayed.  Per-volume tile
 // shapes come from a timing autotuner whose results are cached per process
 // (keyed by device, geometry and direction); the arithmetic of every output
 // sample does not depend on the tile shape, so a volume's iterates are
@@ -353,24 +354,47 @@ static cdv_status batch_tables(cdv_batch* b, const float* const* Y, float* const
     return CDV_OK;
 }
 
-static cdv_status batch_enqueue(cdv_batch* b, int K, const cdv_iter_opts& o, cudaStream_t s)
+struct BatchRun {
+    cdv_batch* b;
+    int K;
+    cdv_iter_opts o;
+};
+
+// Phases of a batched run (see build_loop_graph): 0 prologue, 1 one trial slot for every volume,
+// 2 epilogue.  In a loop graph the slot ends with the loop condition (any volume still running).
+static cdv_status batch_phase(void* vctx, int phase, bool loop, unsigned long long h, cudaStream_t s)
 {
-    BCUDA(launch_batch_x0(b->d_ctx, b->count, o.x0_policy, s), "x0");
-    BCUDA(launch_batch_state_init(b->d_ctx, b->count, o.delta0 > 0.0 ? o.delta0 : 0.0, o.beta, o.max_halvings,
-                                  o.max_rejects, K, kBatchHist, s), "state");
-    for (const auto& g : b->groups)
-        BCUDA(conv_fp32_batch_launch(g.q3, b->d_fwd_init, b->d_items_f + g.off_f, g.n_f, g.smem_f, s), "forward");
-    BCUDA(launch_batch_decide(b->d_ctx, b->count, 1, s), "decide");
-    const int slots = K > 0 ? K + o.max_rejects : 0;
-    for (int i = 0; i < slots; i++) {
+    BatchRun& R = *static_cast<BatchRun*>(vctx);
+    cdv_batch* b = R.b;
+    const int max_trials = R.K + R.o.max_rejects + 1;
+    if (phase == 0) {
+        BCUDA(launch_batch_x0(b->d_ctx, b->count, R.o.x0_policy, s), "x0");
+        BCUDA(launch_batch_state_init(b->d_ctx, b->count, R.o.delta0 > 0.0 ? R.o.delta0 : 0.0, R.o.beta,
+                                      R.o.max_halvings, R.o.max_rejects, R.K, kBatchHist, s), "state");
+        for (const auto& g : b->groups)
+            BCUDA(conv_fp32_batch_launch(g.q3, b->d_fwd_init, b->d_items_f + g.off_f, g.n_f, g.smem_f, s), "forward");
+        BCUDA(launch_batch_decide(b->d_ctx, b->count, 1, s), "decide");
+    } else if (phase == 1) {
         for (const auto& g : b->groups)
             BCUDA(conv_fp32_batch_launch(g.q3, b->d_adj_trial, b->d_items_a + g.off_a, g.n_a, g.smem_a, s), "adjoint");
         for (const auto& g : b->groups)
             BCUDA(conv_fp32_batch_launch(g.q3, b->d_fwd_trial, b->d_items_f + g.off_f, g.n_f, g.smem_f, s), "forward");
         BCUDA(launch_batch_decide(b->d_ctx, b->count, 0, s), "decide");
+    } else {
+        BCUDA(launch_batch_finalize(b->d_ctx, b->count, s), "finalize");
+        return CDV_OK;
     }
-    BCUDA(launch_batch_finalize(b->d_ctx, b->count, s), "finalize");
+    if (loop) BCUDA(launch_batch_loop_cond(b->d_ctx, b->count, h, max_trials, s), "loop condition");
     return CDV_OK;
+}
+
+static cdv_status batch_enqueue(cdv_batch* b, int K, const cdv_iter_opts& o, cudaStream_t s)
+{
+    BatchRun R{b, K, o};
+    cdv_status st = batch_phase(&R, 0, false, 0, s);
+    for (int i = 0; st == CDV_OK && K > 0 && i < K + o.max_rejects; i++) st = batch_phase(&R, 1, false, 0, s);
+    if (st == CDV_OK) st = batch_phase(&R, 2, false, 0, s);
+    return st;
 }
 
 cdv_status cdv_batch_iterate(cdv_batch* b, const float* const* Y, float* const* X, int K, const cdv_iter_opts* opts,
@@ -403,15 +427,10 @@ cdv_status cdv_batch_iterate(cdv_batch* b, const float* const* Y, float* const* 
             b->gexec = nullptr;
             b->graph = nullptr;
             b->key_valid = false;
-            BCUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
-            cdv_status st = batch_enqueue(b, K, o, b->cap);
+            BatchRun R{b, K, o};
             cudaGraph_t gr = nullptr;
-            cudaError_t e = cudaStreamEndCapture(b->cap, &gr);
-            if (st != CDV_OK) {
-                if (gr) cudaGraphDestroy(gr);
-                return st;
-            }
-            if (e != cudaSuccess) return bfail(CDV_ERR_CUDA, "end capture: %s", cudaGetErrorString(e));
+            cdv_status st = build_loop_graph(b->cap, batch_phase, &R, &gr);
+            if (st != CDV_OK) return st;
             b->graph = gr;
             BCUDA(cudaGraphInstantiate(&b->gexec, gr, 0), "instantiate graph");
             b->key_y = ky;

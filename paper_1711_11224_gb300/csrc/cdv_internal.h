@@ -107,6 +107,8 @@ cudaError_t launch_x0(int policy, float* x, const float* y, int64_t m1, int64_t 
 cudaError_t launch_state_init(IterState* st, double delta0, const double* absum, double beta, int max_halvings,
                               int max_rejects, int K, int hist_cap, cudaStream_t s);
 cudaError_t launch_decide(const IterCtx& c, int nparts_f, int nparts_m, int init, cudaStream_t s);
+cudaError_t launch_decide_loop(const IterCtx& c, int nparts_f, int nparts_m, int init, unsigned long long handle,
+                               int max_trials, cudaStream_t s);
 cudaError_t launch_finalize(const IterCtx& c, int64_t nx, cudaStream_t s);
 
 // Batched iteration: per-volume context read by the batched kernels.
@@ -122,6 +124,13 @@ cudaError_t launch_batch_state_init(const BatchVolCtx* v, int count, double delt
                                     int max_rejects, int K, int hist_cap, cudaStream_t s);
 cudaError_t launch_batch_decide(const BatchVolCtx* v, int count, int init, cudaStream_t s);
 cudaError_t launch_batch_finalize(const BatchVolCtx* v, int count, cudaStream_t s);
+cudaError_t launch_batch_loop_cond(const BatchVolCtx* v, int count, unsigned long long handle, int max_trials,
+                                   cudaStream_t s);
+
+// CUDA graph "prologue -> WHILE(body) -> epilogue": `phase` enqueues phase 0 (prologue), 1 (one trial
+// slot; its last kernel sets the loop condition through the handle) or 2 (epilogue) on a stream.
+typedef cdv_status (*PhaseFn)(void* ctx, int phase, bool loop, unsigned long long handle, cudaStream_t s);
+cdv_status build_loop_graph(cudaStream_t cap, PhaseFn phase, void* ctx, cudaGraph_t* out);
 
 // Template preparation (psf.cu).
 cudaError_t launch_flip(const float* h, float* ht, int q1, int q2, int q3, cudaStream_t s);

@@ -169,6 +169,26 @@ __global__ void __launch_bounds__(512) decide_kernel(IterCtx c, int nf, int nm, 
     decide_body(c, nf, nm, init, sh);
 }
 
+// Decision inside a CUDA-graph WHILE loop: after the step rule, the loop continues while the run is
+// not done; max_trials is a hard cap (K + max_rejects + 1) that always ends the loop.
+__global__ void __launch_bounds__(512) decide_loop_kernel(IterCtx c, int nf, int nm, int init,
+                                                          cudaGraphConditionalHandle h, int max_trials)
+{
+    __shared__ double sh[512];
+    decide_body(c, nf, nm, init, sh);
+    if (threadIdx.x == 0) {
+        const IterState* st = c.st;
+        cudaGraphSetConditional(h, (st->done || st->trials >= max_trials) ? 0u : 1u);
+    }
+}
+
+cudaError_t launch_decide_loop(const IterCtx& c, int nparts_f, int nparts_m, int init, unsigned long long handle,
+                               int max_trials, cudaStream_t s)
+{
+    decide_loop_kernel<<<1, 512, 0, s>>>(c, nparts_f, nparts_m, init, (cudaGraphConditionalHandle)handle, max_trials);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_decide(const IterCtx& c, int nparts_f, int nparts_m, int init, cudaStream_t s)
 {
     decide_kernel<<<1, 512, 0, s>>>(c, nparts_f, nparts_m, init);
@@ -246,6 +266,27 @@ __global__ void batch_finalize_kernel(const BatchVolCtx* v)
     const int64_t n = b.m1 * b.m2 * b.m3;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         b.c.x[0][i] = b.c.x[1][i];
+}
+
+// Loop condition of the batched WHILE graph: continue while any volume is still running.
+__global__ void batch_loop_cond_kernel(const BatchVolCtx* v, int count, cudaGraphConditionalHandle h, int max_trials)
+{
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        const IterState* st = v[i].c.st;
+        if (!st->done && st->trials < max_trials) atomicOr(&any, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
+}
+
+cudaError_t launch_batch_loop_cond(const BatchVolCtx* v, int count, unsigned long long handle, int max_trials,
+                                   cudaStream_t s)
+{
+    batch_loop_cond_kernel<<<1, 256, 0, s>>>(v, count, (cudaGraphConditionalHandle)handle, max_trials);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_batch_x0(const BatchVolCtx* v, int count, int policy, cudaStream_t s)
