@@ -160,9 +160,14 @@ static bool tc_config(const cdv_plan* P, const ConvGeom& g, bool fwd, TcArgs& t)
     t.tiles1 = ceil_div(g.b1, t.P);
     t.tiles2 = ceil_div(g.b2, 128 * t.MT);
     t.tiles3 = ceil_div(g.b3, 16);
-    const int64_t grid = (int64_t)t.tiles1 * t.tiles2 * t.tiles3;
-    if (grid > (1LL << 31) - 1 || t.rows / 2 > 256 || t.K > 256) return false;
-    t.grid = (int)grid;
+    const int64_t ntiles = (int64_t)t.tiles1 * t.tiles2 * t.tiles3;
+    if (ntiles > (1LL << 31) - 1 || t.rows / 2 > 256 || t.K > 256) return false;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+        return false;
+    t.ntiles = (int)ntiles;
+    t.grid = (int)std::min<int64_t>(ntiles, nsm);     // one CTA per SM (about 220 KB of shared memory each)
     t.tmem_cols = 512;                      // 2 partial buffers x 16 planes x 16 columns
     t.sh_pitch = fwd ? P->pitch_r : P->pitch_x;
     t.err = P->dev_err;

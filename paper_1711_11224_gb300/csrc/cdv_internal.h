@@ -179,7 +179,9 @@ struct TcArgs {
     int MT;              // 128-row M tiles per CTA
     int rows;            // staged input rows (>= 128*MT + q2 - 1), two TMA boxes of rows/2
     int na, ns;          // input-plane buffers, template-tile stages
-    int tiles1, tiles2, tiles3, grid;
+    int tiles1, tiles2, tiles3;
+    int ntiles;          // output tiles (tiles1 x tiles2 x tiles3)
+    int grid;            // persistent CTAs (at most one per SM), each walking tiles blockIdx.x + k * grid
     unsigned tmem_cols;
     int64_t sh_pitch;    // row pitch of the output shadows
     float* out;          // ROLE_PLAIN output

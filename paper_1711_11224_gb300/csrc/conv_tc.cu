@@ -187,7 +187,7 @@ __device__ __forceinline__ void store_shadow(void* hi, void* lo, int64_t i, floa
 
 // Shared-memory layout of one CTA (bytes).
 struct TcSmem {
-    size_t a_bytes, b_bytes, off_b, off_bar, total;
+    size_t a_bytes, b_bytes, off_b, off_bar, off_stage, total;
     __host__ __device__ static TcSmem make(const TcArgs& t)
     {
         TcSmem s;
@@ -195,12 +195,41 @@ struct TcSmem {
         s.b_bytes = (size_t)t.kchunks * t.P * kN * 16;           // one part of one ring stage
         s.off_b = (size_t)t.na * t.nprec * s.a_bytes;
         s.off_bar = s.off_b + (size_t)t.ns * t.nprec * s.b_bytes;
-        s.total = s.off_bar + 512;
+        s.off_stage = s.off_bar + 512;
+        s.total = s.off_stage + (size_t)(kThreads / 32 - 2) * 32 * kEC * 4;   // 32 x 8 floats per epilogue warp
         return s;
     }
 };
 
 size_t tc_smem_bytes(const TcArgs& t) { return TcSmem::make(t).total + 1024; }
+
+// One output tile: planes [S1, S1 + P), rows [S2, S2 + 128), columns [S3, S3 + 16), and the input
+// planes [ulo, uhi] that reach it.
+struct TcTile {
+    int64_t S1, S2, S3, s1_end, ulo, uhi;
+    __device__ static TcTile make(const TcArgs& T, int tile)
+    {
+        TcTile c;
+        const int t3 = tile % T.tiles3;
+        tile /= T.tiles3;
+        const int t2 = tile % T.tiles2;
+        const int t1 = tile / T.tiles2;
+        const ConvGeom& G = T.g;
+        c.S1 = (int64_t)t1 * kP;
+        c.S2 = (int64_t)t2 * kM * kMT;
+        c.S3 = (int64_t)t3 * kN;
+        c.s1_end = min(c.S1 + kP, G.b1);
+        c.ulo = max((int64_t)0, c.S1 + G.o1 - G.q1 + 1);
+        c.uhi = min(G.a1 - 1, c.s1_end - 1 + G.o1);
+        return c;
+    }
+    // output planes of the tile that input plane u reaches: [ilo, ihi] (relative to S1)
+    __device__ void plane_range(const ConvGeom& G, int64_t u, int& ilo, int& ihi) const
+    {
+        ilo = (int)max((int64_t)0, u - G.o1 - S1);
+        ihi = (int)min(s1_end - 1 - S1, u - G.o1 + G.q1 - 1 - S1);
+    }
+};
 
 template <int KIND>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -215,13 +244,6 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
     const TcSmem lay = TcSmem::make(T);
     const ConvGeom& G = T.g;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-
-    int bt = blockIdx.x;
-    const int t3 = bt % T.tiles3;
-    bt /= T.tiles3;
-    const int t2 = bt % T.tiles2;
-    const int t1 = bt / T.tiles2;
-    const int64_t S1 = (int64_t)t1 * kP, S2 = (int64_t)t2 * kM * kMT, S3 = (int64_t)t3 * kN;
 
     const int role = T.role;
     int sel = 0, cur = 0;
@@ -264,11 +286,11 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
     unsigned* tslot = reinterpret_cast<unsigned*>(sm + lay.off_bar + 384);
     volatile int* sflag = reinterpret_cast<volatile int*>(sm + lay.off_bar + 392);
 
-    // input planes reaching the CTA's output planes [S1, min(S1 + P, b1))
-    const int64_t s1_end = min(S1 + kP, G.b1);
-    const int64_t ulo = max((int64_t)0, S1 + G.o1 - G.q1 + 1);
-    const int64_t uhi = min(G.a1 - 1, s1_end - 1 + G.o1);
-    const bool have_work = do_conv && ulo <= uhi && *(volatile int*)T.err == 0;
+    // Persistent CTAs: tiles blockIdx.x, blockIdx.x + gridDim.x, ...  Every role walks the same
+    // sequence and keeps its ring and accumulator counters across tiles, so the epilogue of one
+    // tile overlaps the loads and MMAs of the next.
+    const int ntiles = T.ntiles;
+    const bool run = do_conv && *(volatile int*)T.err == 0;
 
     if (tid == 0) {
         for (int i = 0; i < 38; i++) mbar_init(bar0 + 8u * i, 1);
@@ -279,7 +301,7 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     const unsigned tcols = T.tmem_cols;
-    if (have_work && warp == 0) {
+    if (run && warp == 0) {
         __syncwarp();
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tslot)), "r"(tcols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
@@ -287,57 +309,56 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    const unsigned tmem = have_work ? *tslot : 0u;
+    const unsigned tmem = run ? *tslot : 0u;
 
-    const int64_t ws = S3 + G.o3 - (G.q3 - 1) - T.e;             // input column of K index 0
-    const int64_t v0 = S2 + G.o2 - (G.q2 - 1);                    // input row of staged row 0
     const int half = T.rows / 2;
     const int ksteps = T.K / (2 * EPT);
-    // output planes of the CTA that input plane u reaches: [ilo, ihi] (relative to S1)
-    auto plane_range = [&](int64_t u, int& ilo, int& ihi) {
-        ilo = (int)max((int64_t)0, u - G.o1 - S1);
-        ihi = (int)min(s1_end - 1 - S1, u - G.o1 + G.q1 - 1 - S1);
-    };
     auto fail = [&]() {
         *sflag = 1;
         atomicExch(T.err, (int)CDV_ERR_TIMEOUT);
     };
 
-    if (have_work && warp == 0 && lane == 0) {
+    if (run && warp == 0 && lane == 0) {
         // ---------------- TMA producer
         int bs = 0, it = 0, nb = 0;
         unsigned bph = 0;
         int a_uses[2] = {0, 0};
-        for (int64_t u = ulo; u <= uhi && !*sflag; ++u, ++it) {
-            const int ab = it % T.na;
-            if (!mbar_wait(A_EMPTY(ab), (unsigned)(((it / T.na) & 1) ^ 1))) { fail(); break; }
-            mbar_expect_tx(A_FULL(ab), (unsigned)(NPREC * lay.a_bytes));
-            a_uses[ab] = it / T.na + 1;
-            for (int p = 0; p < NPREC; p++) {
-                const CUtensorMap* mp = p ? map_lo : map_hi;
-                const unsigned dst = su32(sA + ((size_t)ab * NPREC + p) * lay.a_bytes);
-                for (int c = 0; c < T.kchunks; c++)
-                    for (int h = 0; h < 2; h++)
-                        tma3(dst + (unsigned)((c * T.rows + h * half) * 16), mp, (int)(ws + c * EPT), (int)(v0 + h * half),
-                             (int)u, A_FULL(ab));
-            }
-            int ilo, ihi;
-            plane_range(u, ilo, ihi);
-            const int64_t j1lo = S1 + ilo + G.o1 - u;
-            const int nv = ihi - ilo + 1;
-            for (int j2 = 0; j2 < G.q2; j2++) {
-                if (!mbar_wait(B_EMPTY(bs), bph ^ 1)) { fail(); break; }
-                mbar_expect_tx(B_FULL(bs), (unsigned)(NPREC * T.kchunks * nv * kN * 16));
+        for (int tile = blockIdx.x; tile < ntiles && !*sflag; tile += gridDim.x) {
+            const TcTile C = TcTile::make(T, tile);
+            const int64_t ws = C.S3 + G.o3 - (G.q3 - 1) - T.e;      // input column of K index 0
+            const int64_t v0 = C.S2 + G.o2 - (G.q2 - 1);            // input row of staged row 0
+            for (int64_t u = C.ulo; u <= C.uhi && !*sflag; ++u, ++it) {
+                const int ab = it % T.na;
+                if (!mbar_wait(A_EMPTY(ab), (unsigned)(((it / T.na) & 1) ^ 1))) { fail(); break; }
+                mbar_expect_tx(A_FULL(ab), (unsigned)(NPREC * lay.a_bytes));
+                a_uses[ab] = it / T.na + 1;
                 for (int p = 0; p < NPREC; p++) {
-                    const unsigned char* src0 = reinterpret_cast<const unsigned char*>(T.bt[p]);
-                    const unsigned dst = su32(sB + ((size_t)bs * NPREC + p) * lay.b_bytes);
-                    for (int c = 0; c < T.kchunks; c++) {
-                        const size_t row = ((size_t)j2 * T.kchunks + c) * G.q1 * kN + (size_t)j1lo * kN;
-                        bulk_g2s(dst + (unsigned)(c * T.P * kN * 16), src0 + row * 16, (unsigned)(nv * kN * 16), B_FULL(bs));
-                    }
+                    const CUtensorMap* mp = p ? map_lo : map_hi;
+                    const unsigned dst = su32(sA + ((size_t)ab * NPREC + p) * lay.a_bytes);
+                    for (int c = 0; c < T.kchunks; c++)
+                        for (int h = 0; h < 2; h++)
+                            tma3(dst + (unsigned)((c * T.rows + h * half) * 16), mp, (int)(ws + c * EPT),
+                                 (int)(v0 + h * half), (int)u, A_FULL(ab));
                 }
-                ++nb;
-                if (++bs == T.ns) { bs = 0; bph ^= 1; }
+                int ilo, ihi;
+                C.plane_range(G, u, ilo, ihi);
+                const int64_t j1lo = C.S1 + ilo + G.o1 - u;
+                const int nv = ihi - ilo + 1;
+                for (int j2 = 0; j2 < G.q2; j2++) {
+                    if (!mbar_wait(B_EMPTY(bs), bph ^ 1)) { fail(); break; }
+                    mbar_expect_tx(B_FULL(bs), (unsigned)(NPREC * T.kchunks * nv * kN * 16));
+                    for (int p = 0; p < NPREC; p++) {
+                        const unsigned char* src0 = reinterpret_cast<const unsigned char*>(T.bt[p]);
+                        const unsigned dst = su32(sB + ((size_t)bs * NPREC + p) * lay.b_bytes);
+                        for (int c = 0; c < T.kchunks; c++) {
+                            const size_t row = ((size_t)j2 * T.kchunks + c) * G.q1 * kN + (size_t)j1lo * kN;
+                            bulk_g2s(dst + (unsigned)(c * T.P * kN * 16), src0 + row * 16, (unsigned)(nv * kN * 16),
+                                     B_FULL(bs));
+                        }
+                    }
+                    ++nb;
+                    if (++bs == T.ns) { bs = 0; bph ^= 1; }
+                }
             }
         }
         // make sure every copy this thread issued has landed before the CTA may exit
@@ -347,56 +368,60 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
             const int idx = nb - 1 - k;                           // the last use of each stage
             mbar_wait(B_FULL(idx % T.ns), (unsigned)((idx / T.ns) & 1));
         }
-    } else if (have_work && warp == 1 && lane == 0) {
+    } else if (run && warp == 1 && lane == 0) {
         // ---------------- MMA issuer
         const unsigned fmt = (KIND == CDV_MODE_TF32) ? 2u : 1u;
         const unsigned lbo_a = (unsigned)T.rows * 16, lbo_b = (unsigned)T.P * kN * 16;
         int bs = 0, it = 0;
         unsigned bph = 0;
         bool ok = true;
-        for (int64_t u = ulo; u <= uhi && ok && !*sflag; ++u, ++it) {
-            const int b = it & 1;
-            if (it >= 2 && !mbar_wait(ACC_FREE(b), (unsigned)(((it >> 1) - 1) & 1))) { ok = false; break; }
-            const int ab = it % T.na;
-            if (!mbar_wait(A_FULL(ab), (unsigned)((it / T.na) & 1))) { ok = false; break; }
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            int ilo, ihi;
-            plane_range(u, ilo, ihi);
-            const unsigned n = (unsigned)(kN * (ihi - ilo + 1));
-            const unsigned idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((n >> 3) << 17) | ((unsigned)(kM >> 4) << 24);
-            const unsigned a_hi = su32(sA + ((size_t)ab * NPREC + 0) * lay.a_bytes);
-            const unsigned a_lo = su32(sA + ((size_t)ab * NPREC + (NPREC - 1)) * lay.a_bytes);
-            for (int j2 = 0; j2 < G.q2; j2++) {
-                if (!mbar_wait(B_FULL(bs), bph)) { ok = false; break; }
+        for (int tile = blockIdx.x; tile < ntiles && ok && !*sflag; tile += gridDim.x) {
+            const TcTile C = TcTile::make(T, tile);
+            for (int64_t u = C.ulo; u <= C.uhi && ok && !*sflag; ++u, ++it) {
+                const int b = it & 1;
+                if (it >= 2 && !mbar_wait(ACC_FREE(b), (unsigned)(((it >> 1) - 1) & 1))) { ok = false; break; }
+                const int ab = it % T.na;
+                if (!mbar_wait(A_FULL(ab), (unsigned)((it / T.na) & 1))) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                const unsigned b_hi = su32(sB + ((size_t)bs * NPREC + 0) * lay.b_bytes);
-                const unsigned b_lo = su32(sB + ((size_t)bs * NPREC + (NPREC - 1)) * lay.b_bytes);
-                const unsigned arow = (unsigned)(G.q2 - 1 - j2) * 16u;
-                for (int k = 0; k < ksteps; k++) {
-                    const uint64_t bd_hi = sdesc(b_hi + 2u * k * lbo_b, lbo_b, 128);
-                    const uint64_t bd_lo = sdesc(b_lo + 2u * k * lbo_b, lbo_b, 128);
-                    for (int mt = 0; mt < kMT; mt++) {
-                        if (S2 + (int64_t)mt * kM >= G.b2) break;
-                        const unsigned aoff = 2u * k * lbo_a + arow + (unsigned)(mt * kM * 16);
-                        const unsigned d = tmem + (unsigned)(((mt * 2 + b) * T.P + ilo) * kN);
-                        const unsigned acc = (j2 == 0 && k == 0) ? 0u : 1u;   // fresh partial per input plane
-                        const uint64_t ad_hi = sdesc(a_hi + aoff, lbo_a, 128);
-                        if (KIND == CDV_MODE_SPLIT_BF16X3) {
-                            // hi*hi and hi*lo share A: the second reuses it from the collector buffer
-                            mma_bf16_fill(d, ad_hi, bd_hi, idesc, acc);
-                            mma_bf16_lastuse(d, ad_hi, bd_lo, idesc, 1u);
-                            mma<KIND>(d, sdesc(a_lo + aoff, lbo_a, 128), bd_hi, idesc, 1u);
-                        } else {
-                            mma<KIND>(d, ad_hi, bd_hi, idesc, acc);
+                int ilo, ihi;
+                C.plane_range(G, u, ilo, ihi);
+                const unsigned n = (unsigned)(kN * (ihi - ilo + 1));
+                const unsigned idesc =
+                    (1u << 4) | (fmt << 7) | (fmt << 10) | ((n >> 3) << 17) | ((unsigned)(kM >> 4) << 24);
+                const unsigned a_hi = su32(sA + ((size_t)ab * NPREC + 0) * lay.a_bytes);
+                const unsigned a_lo = su32(sA + ((size_t)ab * NPREC + (NPREC - 1)) * lay.a_bytes);
+                for (int j2 = 0; j2 < G.q2; j2++) {
+                    if (!mbar_wait(B_FULL(bs), bph)) { ok = false; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    const unsigned b_hi = su32(sB + ((size_t)bs * NPREC + 0) * lay.b_bytes);
+                    const unsigned b_lo = su32(sB + ((size_t)bs * NPREC + (NPREC - 1)) * lay.b_bytes);
+                    const unsigned arow = (unsigned)(G.q2 - 1 - j2) * 16u;
+                    for (int k = 0; k < ksteps; k++) {
+                        const uint64_t bd_hi = sdesc(b_hi + 2u * k * lbo_b, lbo_b, 128);
+                        const uint64_t bd_lo = sdesc(b_lo + 2u * k * lbo_b, lbo_b, 128);
+                        for (int mt = 0; mt < kMT; mt++) {
+                            if (C.S2 + (int64_t)mt * kM >= G.b2) break;
+                            const unsigned aoff = 2u * k * lbo_a + arow + (unsigned)(mt * kM * 16);
+                            const unsigned d = tmem + (unsigned)(((mt * 2 + b) * T.P + ilo) * kN);
+                            const unsigned acc = (j2 == 0 && k == 0) ? 0u : 1u;   // fresh partial per input plane
+                            const uint64_t ad_hi = sdesc(a_hi + aoff, lbo_a, 128);
+                            if (KIND == CDV_MODE_SPLIT_BF16X3) {
+                                // hi*hi and hi*lo share A: the second reuses it from the collector buffer
+                                mma_bf16_fill(d, ad_hi, bd_hi, idesc, acc);
+                                mma_bf16_lastuse(d, ad_hi, bd_lo, idesc, 1u);
+                                mma<KIND>(d, sdesc(a_lo + aoff, lbo_a, 128), bd_hi, idesc, 1u);
+                            } else {
+                                mma<KIND>(d, ad_hi, bd_hi, idesc, acc);
+                            }
                         }
                     }
+                    mma_commit(B_EMPTY(bs));
+                    if (++bs == T.ns) { bs = 0; bph ^= 1; }
                 }
-                mma_commit(B_EMPTY(bs));
-                if (++bs == T.ns) { bs = 0; bph ^= 1; }
+                if (!ok) break;
+                mma_commit(A_EMPTY(ab));
+                mma_commit(ACC_FULL(b));
             }
-            if (!ok) break;
-            mma_commit(A_EMPTY(ab));
-            mma_commit(ACC_FULL(b));
         }
         if (!ok) fail();
         mma_commit(DRAIN);                                        // completes when every issued MMA has
@@ -409,53 +434,65 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
     if (warp >= 2) {
         const int cg = (warp - 2) >> 2;
         const int quarter = warp & 3;
-        const int m = quarter * 32 + lane;
-        const int64_t s2 = S2 + m;
-        float tot[kP][kEC];
-#pragma unroll
-        for (int i = 0; i < kP; i++)
-#pragma unroll
-            for (int c = 0; c < kEC; c++) tot[i][c] = 0.f;
+        float* stg = reinterpret_cast<float*>(sm + lay.off_stage) + (warp - 2) * 32 * kEC;
+        float4* stg4 = reinterpret_cast<float4*>(stg);
         bool ok = true;
-        if (have_work) {
-            int it = 0;
-            for (int64_t u = ulo; u <= uhi; ++u, ++it) {
-                const int b = it & 1;
-                bool w = mbar_wait(ACC_FULL(b), (unsigned)((it >> 1) & 1));
-                w = __all_sync(0xffffffffu, w && !*sflag);
-                if (!w) {
-                    ok = false;
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                int ilo, ihi;
-                plane_range(u, ilo, ihi);
+        int it = 0;
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            const TcTile C = TcTile::make(T, tile);
+            float tot[kP][kEC];
 #pragma unroll
-                for (int i = 0; i < kP; i++) {
-                    if (i < ilo || i > ihi) continue;                 // warp-uniform
-                    float v[kEC];
-                    tmem_ld8(tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)((b * T.P + i) * kN + cg * kEC), v);
+            for (int i = 0; i < kP; i++)
 #pragma unroll
-                    for (int c = 0; c < kEC; c++) tot[i][c] += v[c];
+                for (int c = 0; c < kEC; c++) tot[i][c] = 0.f;
+            if (run) {
+                for (int64_t u = C.ulo; u <= C.uhi; ++u, ++it) {
+                    const int b = it & 1;
+                    bool w = mbar_wait(ACC_FULL(b), (unsigned)((it >> 1) & 1));
+                    w = __all_sync(0xffffffffu, w && !*sflag);
+                    if (!w) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    int ilo, ihi;
+                    C.plane_range(G, u, ilo, ihi);
+#pragma unroll
+                    for (int i = 0; i < kP; i++) {
+                        if (i < ilo || i > ihi) continue;                 // warp-uniform
+                        float v[kEC];
+                        tmem_ld8(tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)((b * T.P + i) * kN + cg * kEC),
+                                 v);
+#pragma unroll
+                        for (int c = 0; c < kEC; c++) tot[i][c] += v[c];
+                    }
+                    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(ACC_FREE(b));
                 }
-                asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-                __syncwarp();
-                if (lane == 0) mbar_arrive(ACC_FREE(b));
             }
-        }
-        if (!ok && lane == 0) fail();
-        if (ok && s2 < G.b2) {
+            if (!ok) break;
+            // Stores go through a per-warp 32 x 8 staging tile so that each warp instruction touches
+            // four output rows of 8 consecutive columns instead of 32 rows of one column.  Row r's two
+            // 16-byte halves swap places when bit 2 of r is set: conflict-free on both sides.
 #pragma unroll
             for (int i = 0; i < kP; i++) {
-                const int64_t s1 = S1 + i;
-                if (s1 >= G.b1) continue;
+                const int64_t s1 = C.S1 + i;
+                if (s1 >= G.b1) continue;                                 // warp-uniform
+                __syncwarp();
+                const int sw = (lane >> 2) & 1;
+                stg4[lane * 2 + sw] = make_float4(tot[i][0], tot[i][1], tot[i][2], tot[i][3]);
+                stg4[lane * 2 + (sw ^ 1)] = make_float4(tot[i][4], tot[i][5], tot[i][6], tot[i][7]);
+                __syncwarp();
 #pragma unroll
-                for (int c = 0; c < kEC; c++) {
-                    const int64_t s3 = S3 + cg * kEC + c;
-                    if (s3 >= G.b3) continue;
+                for (int k = 0; k < 8; k++) {
+                    const int r = k * 4 + (lane >> 3), c = lane & 7;
+                    const float v = stg[r * 8 + ((((c >> 2) ^ (k & 1))) << 2) + (c & 3)];
+                    const int64_t s2 = C.S2 + quarter * 32 + r;
+                    const int64_t s3 = C.S3 + cg * kEC + c;
+                    if (s2 >= G.b2 || s3 >= G.b3) continue;
                     const int64_t idx = (s1 * G.b2 + s2) * G.b3 + s3;
                     const int64_t sidx = (s1 * G.b2 + s2) * T.sh_pitch + s3;
-                    const float v = tot[i][c];
                     switch (role) {
                     case ROLE_PLAIN:
                         out[idx] = v;
@@ -490,6 +527,7 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
                 }
             }
         }
+        if (!ok && lane == 0) fail();
     }
 
     // ---------------- block partial of the norm, teardown
@@ -508,7 +546,7 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
         double* part = (role == ROLE_ADJ_TRIAL) ? T.ctx.part_m : T.ctx.part_f;
         part[blockIdx.x] = t;
     }
-    if (have_work && warp == 0) {
+    if (run && warp == 0) {
         __syncwarp();
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tcols));

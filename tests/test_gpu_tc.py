@@ -36,6 +36,7 @@ SHAPES = [
     ((3, 20, 300), (1, 3, 5)),        # output rows wider than one CTA (two column groups)
     ((50, 70), (7, 7)),               # n = 2
     ((3, 4, 5), (7, 9, 11)),          # template larger than the volume
+    ((60, 400, 300), (3, 5, 7)),      # 320 forward tiles: several tiles per persistent CTA
 ]
 
 
@@ -82,6 +83,20 @@ def test_tc_iterate(mode):
     assert rel_l2(Xg, ref["X"]) <= tol
     # f = 1/2 ||Ax - y||^2: the residual cancels, so its relative error exceeds the per-convolution one
     np.testing.assert_allclose(rep["f"], ref["f"], rtol=1e-4 if mode == "split3" else 2e-3)
+
+
+def test_tc_iterate_many_tiles():
+    """More output tiles than SMs, so each persistent CTA carries its rings across tiles."""
+    from paper_1711_11224_gb300 import Plan
+    P = synth.scaled_fil3d((40, 300, 260), (5, 5, 7), K=5)
+    with Plan(P.m, P.p, mode="split3") as pl:
+        pl.set_psf(_dev(P.H))
+        X, rep = pl.iterate(_dev(P.Y), K=5, x0="crop")
+        Xg = X.cpu().numpy()
+    ref = oracle.iterate(P.Y, P.H, oracle.x0_crop(P.Y, P.p), 5)
+    assert rep["accepted"] == 5 and rep["status"] == "CDV_OK"
+    assert rel_l2(Xg, ref["X"]) <= TOL_ITER
+    np.testing.assert_allclose(rep["f"], ref["f"], rtol=1e-4)
 
 
 def test_tc_graph_matches_stream():
