@@ -154,8 +154,8 @@ static bool tc_config(const cdv_plan* P, const ConvGeom& g, bool fwd, TcArgs& t)
     t.e = ((off % ept) + ept) % ept;
     t.K = (t.e + g.q3 + 15 + 15) / 16 * 16;
     t.kchunks = t.K / ept;
-    t.P = 16;
-    t.MT = 1;
+    t.P = 8;
+    t.MT = 2;
     t.rows = (128 * t.MT + g.q2 - 1 + 15) / 16 * 16;
     t.tiles1 = ceil_div(g.b1, t.P);
     t.tiles2 = ceil_div(g.b2, 128 * t.MT);
@@ -168,7 +168,7 @@ static bool tc_config(const cdv_plan* P, const ConvGeom& g, bool fwd, TcArgs& t)
         return false;
     t.ntiles = (int)ntiles;
     t.grid = (int)std::min<int64_t>(ntiles, nsm);     // one CTA per SM (about 220 KB of shared memory each)
-    t.tmem_cols = 512;                      // 2 partial buffers x 16 planes x 16 columns
+    t.tmem_cols = 512;                      // 2 partial buffers x 2 M tiles x 8 planes x 16 columns
     t.sh_pitch = fwd ? P->pitch_r : P->pitch_x;
     t.err = P->dev_err;
     // deepest template-tile ring that fits: each stage is one template row of one input plane

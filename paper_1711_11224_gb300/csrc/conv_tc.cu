@@ -10,37 +10,46 @@
 //     D_{s1}[row, n] += A_{u, j2}[row, k] * T_{s1+o1-u, j2}[k, n]
 // where A_{u, j2} is input plane u read at rows shifted by j2.
 //
-// Shapes chosen for the tensor pipe (an M128 x K16 MMA costs about
-// max(46, N/2) cycles, so N must be large):
+// Shapes chosen for the tensor pipe and for the supply of template tiles:
 //  * N = 16 x (output planes): one input plane u and template row j2 feed the
-//    CTA's P = 16 output planes through Toeplitz tiles of consecutive j1,
+//    CTA's P = 8 output planes through Toeplitz tiles of consecutive j1,
 //    which are stored side by side ([j2][K chunk][j1*16 + n]), so one MMA
-//    with N = 16 x (planes in range) <= 256 updates all of them.
-//  * M = 128 rows per CTA.  Split-BF16x3 issues hi*hi and hi*lo back to back
-//    with the A operand kept in the tensor core's collector buffer, so A is
-//    read from shared memory twice per three products.
+//    with N = 16 x (planes in range) <= 128 updates all of them.
+//  * Two M tiles of 128 rows per CTA: every template-tile stage (24 KB for
+//    split-BF16x3 with K = 48) feeds both, which halves the template bytes
+//    streamed from L2 per MMA; the stages were the limiter with one M tile.
+//    Split-BF16x3 issues hi*hi and hi*lo back to back with the A operand kept
+//    in the tensor core's collector buffer, so A is read from shared memory
+//    twice per three products.
 //  * The row shift j2 is a 16-byte shift of the shared-memory descriptor of
 //    one TMA-staged tile of plane u (K-major, no swizzle: core matrices of
 //    8 rows x 16 bytes, rows 16 bytes apart), so the tile serves all q2 rows.
 //  * Two-level accumulation: the contribution of each input plane goes to a
-//    fresh TMEM partial (two buffers), which epilogue warps add into FP32
-//    register totals while the MMAs of the next plane run.  One TMEM
-//    accumulator over all q1*q2 template rows drifts (the tensor core's FP32
-//    accumulation truncates): 1e-4 relative for a 31x31x21 template.
+//    fresh TMEM partial (two buffers x two M tiles x 8 planes x 16 columns =
+//    all 512 columns), which epilogue warps add into FP32 register totals
+//    while the MMAs of the next plane run.  One TMEM accumulator over all
+//    q1*q2 template rows drifts (the tensor core's FP32 accumulation
+//    truncates): 1e-4 relative for a 31x31x21 template.
+//  * Persistent CTAs, one per SM, walk the output tiles with their ring and
+//    accumulator counters carried across tiles, so a tile's stores overlap
+//    the next tile's loads and MMAs.
 //
 // Warp roles (320 threads):
 //   warp 0      TMA producer: per input plane, the A tile (per 16-byte K chunk
 //               two boxes of rows/2 rows, zero-filled outside the volume) and,
 //               per template row, the Toeplitz tiles of the planes in range
-//               (bulk copies through a 4-stage ring).
-//   warp 1      MMA issuer (one thread): per (j2, K step) one MMA, three
-//               for split-BF16x3 (hi*hi, hi*lo, lo*hi); tcgen05.commit
-//               releases ring stages and hands each plane's partial to the
-//               epilogue.
-//   warps 2-9   epilogue, one output row per thread, each warpgroup owning 8 of
-//               the 16 columns: drains the partials, then the fused epilogue
-//               of the FP32 engine plus the BF16/TF32 shadows the next
-//               convolution reads.
+//               (bulk copies through a ring of stages).
+//   warp 1      MMA issuer: the whole warp runs the loop with warp-uniform
+//               descriptors and one elected lane issues each MMA (three for
+//               split-BF16x3); tcgen05.commit releases ring stages and hands
+//               each plane's partial to the epilogue.  A single thread
+//               computing its own descriptors issued an MMA only every ~90
+//               cycles, slower than the tensor pipe at N = 128.
+//   warps 2-9   epilogue, one output row per thread, warpgroup g owning M
+//               tile g: drains the partials, then the fused epilogue of the
+//               FP32 engine plus the BF16/TF32 shadows the next convolution
+//               reads, stored through a per-warp staging tile so that warp
+//               accesses cover rows of 8 consecutive columns.
 // Every wait is bounded (about 0.5 s).  A wait that runs out records
 // CDV_ERR_TIMEOUT in the device error word; the CTA stops issuing work, waits
 // for its own copies and MMAs, frees its TMEM and exits.  CTAs that start
@@ -59,8 +68,8 @@ namespace {
 
 constexpr int kM = 128;
 constexpr int kN = 16;
-constexpr int kP = 16;         // output planes per CTA (N of one MMA up to 256)
-constexpr int kMT = 1;         // M tiles per CTA
+constexpr int kP = 8;          // output planes per CTA (N of one MMA up to 128)
+constexpr int kMT = 2;         // 128-row M tiles per CTA: each template-tile stage feeds both
 constexpr int kEC = 8;         // accumulator columns per plane drained by one epilogue warpgroup
 constexpr int kThreads = 320;
 
@@ -81,17 +90,21 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
 }
 // Bounded wait for the phase of the given parity; false after ~1e9 cycles (~0.5 s).
+__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
 __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity)
 {
+    if (mbar_try(bar, parity)) return true;                        // fast path: no clock reads
     const long long t0 = clock64();
     for (;;) {
-        unsigned ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (ok) return true;
+        if (mbar_try(bar, parity)) return true;
         if (clock64() - t0 > 1000000000ll) return false;
     }
 }
@@ -109,50 +122,42 @@ __device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned
                  "l"(src), "r"(bytes), "r"(bar)
                  : "memory");
 }
-// BF16 MMA that loads A into the collector buffer (fill) or reuses it and frees it (lastuse).
-__device__ __forceinline__ void mma_bf16_fill(unsigned d, uint64_t a, uint64_t b, unsigned idesc, unsigned acc)
-{
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, "
-        "%3, p;\n}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-__device__ __forceinline__ void mma_bf16_lastuse(unsigned d, uint64_t a, uint64_t b, unsigned idesc, unsigned acc)
-{
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, "
-        "%2, %3, p;\n}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
+// One K step of the product on the tensor core, issued by one elected lane of a converged warp
+// (the operands are warp-uniform).  Split-BF16x3: hi*hi and hi*lo share A, the second reusing it
+// from the collector buffer, then lo*hi.
 template <int KIND>
-__device__ __forceinline__ void mma(unsigned d, uint64_t a, uint64_t b, unsigned idesc, unsigned acc)
+__device__ __forceinline__ void mma_step(unsigned d, uint64_t ah, uint64_t al, uint64_t bh, uint64_t bl, unsigned idesc,
+                                         unsigned acc)
 {
-    if (KIND == CDV_MODE_TF32)
+    if (KIND == CDV_MODE_SPLIT_BF16X3)
         asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+            "{\n .reg .pred p, q, e;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 p, %6, 0;\n setp.ne.b32 q, 1, 0;\n"
+            " @e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %3, %5, p;\n"
+            " @e tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %4, %5, q;\n"
+            " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %3, %5, q;\n}\n" ::"r"(d),
+            "l"(ah), "l"(al), "l"(bh), "l"(bl), "r"(idesc), "r"(acc));
+    else if (KIND == CDV_MODE_TF32)
+        asm volatile(
+            "{\n .reg .pred p, e;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 p, %4, 0;\n"
+            " @e tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+            "l"(ah), "l"(bh), "r"(idesc), "r"(acc));
     else
         asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+            "{\n .reg .pred p, e;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 p, %4, 0;\n"
+            " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+            "l"(ah), "l"(bh), "r"(idesc), "r"(acc));
+}
+// tcgen05.commit from the elected lane (the one that issued the MMAs)
+__device__ __forceinline__ void mma_commit_elect(unsigned bar)
+{
+    asm volatile(
+        "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+        " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(bar)
+        : "memory");
 }
 __device__ __forceinline__ void mbar_arrive(unsigned bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void mma_commit(unsigned bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void tmem_ld8(unsigned taddr, float* v)
-{
-    unsigned r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 8; i++) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tmem_ld16(unsigned taddr, float* v)
 {
@@ -368,71 +373,77 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
             const int idx = nb - 1 - k;                           // the last use of each stage
             mbar_wait(B_FULL(idx % T.ns), (unsigned)((idx / T.ns) & 1));
         }
-    } else if (run && warp == 1 && lane == 0) {
-        // ---------------- MMA issuer
+    } else if (run && warp == 1) {
+        // ---------------- MMA issuer: the whole warp runs the loop (all values warp-uniform) and one
+        // elected lane issues each MMA and commit.  Descriptors are templates with a zero start
+        // address plus the start in 16-byte units, which cannot carry out of the 14-bit field for
+        // shared-memory addresses below 256 KB.
         const unsigned fmt = (KIND == CDV_MODE_TF32) ? 2u : 1u;
         const unsigned lbo_a = (unsigned)T.rows * 16, lbo_b = (unsigned)T.P * kN * 16;
+        const uint64_t da0 = sdesc(0, lbo_a, 128), db0 = sdesc(0, lbo_b, 128);
+        const uint64_t a_kstep = (2u * lbo_a) >> 4, b_kstep = (2u * lbo_b) >> 4;
+        const unsigned sA16 = su32(sA) >> 4, sB16 = su32(sB) >> 4;
+        const unsigned a_part16 = (unsigned)(lay.a_bytes >> 4), b_part16 = (unsigned)(lay.b_bytes >> 4);
         int bs = 0, it = 0;
         unsigned bph = 0;
         bool ok = true;
-        for (int tile = blockIdx.x; tile < ntiles && ok && !*sflag; tile += gridDim.x) {
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
             const TcTile C = TcTile::make(T, tile);
-            for (int64_t u = C.ulo; u <= C.uhi && ok && !*sflag; ++u, ++it) {
+            const int nmt = (int)min((int64_t)kMT, (G.b2 - C.S2 + kM - 1) / kM);   // M tiles holding output rows
+            for (int64_t u = C.ulo; u <= C.uhi; ++u, ++it) {
                 const int b = it & 1;
-                if (it >= 2 && !mbar_wait(ACC_FREE(b), (unsigned)(((it >> 1) - 1) & 1))) { ok = false; break; }
                 const int ab = it % T.na;
-                if (!mbar_wait(A_FULL(ab), (unsigned)((it / T.na) & 1))) { ok = false; break; }
+                bool w = it < 2 || mbar_wait(ACC_FREE(b), (unsigned)(((it >> 1) - 1) & 1));
+                w = w && mbar_wait(A_FULL(ab), (unsigned)((it / T.na) & 1));
+                if (!__all_sync(0xffffffffu, w && !*sflag)) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 int ilo, ihi;
                 C.plane_range(G, u, ilo, ihi);
                 const unsigned n = (unsigned)(kN * (ihi - ilo + 1));
                 const unsigned idesc =
                     (1u << 4) | (fmt << 7) | (fmt << 10) | ((n >> 3) << 17) | ((unsigned)(kM >> 4) << 24);
-                const unsigned a_hi = su32(sA + ((size_t)ab * NPREC + 0) * lay.a_bytes);
-                const unsigned a_lo = su32(sA + ((size_t)ab * NPREC + (NPREC - 1)) * lay.a_bytes);
+                const unsigned d = tmem + (unsigned)((b * T.P + ilo) * kN);
+                // A of this plane, first row of the shift for j2 = 0 (q2 - 1 rows down)
+                const unsigned a_hi = sA16 + (unsigned)(ab * NPREC) * a_part16 + (unsigned)(G.q2 - 1);
+                const unsigned a_lo = a_hi + (unsigned)(NPREC - 1) * a_part16;
+                unsigned acc = 0;                                          // fresh partial per input plane
                 for (int j2 = 0; j2 < G.q2; j2++) {
-                    if (!mbar_wait(B_FULL(bs), bph)) { ok = false; break; }
+                    if (!__all_sync(0xffffffffu, mbar_wait(B_FULL(bs), bph))) { ok = false; break; }
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                    const unsigned b_hi = su32(sB + ((size_t)bs * NPREC + 0) * lay.b_bytes);
-                    const unsigned b_lo = su32(sB + ((size_t)bs * NPREC + (NPREC - 1)) * lay.b_bytes);
-                    const unsigned arow = (unsigned)(G.q2 - 1 - j2) * 16u;
+                    const unsigned b_hi = sB16 + (unsigned)(bs * NPREC) * b_part16;
+                    const uint64_t bh = db0 + b_hi, bl = db0 + b_hi + (unsigned)(NPREC - 1) * b_part16;
+                    const uint64_t ah = da0 + (a_hi - (unsigned)j2), al = da0 + (a_lo - (unsigned)j2);
+#pragma unroll 4
                     for (int k = 0; k < ksteps; k++) {
-                        const uint64_t bd_hi = sdesc(b_hi + 2u * k * lbo_b, lbo_b, 128);
-                        const uint64_t bd_lo = sdesc(b_lo + 2u * k * lbo_b, lbo_b, 128);
+                        const uint64_t ka = (uint64_t)k * a_kstep, kb = (uint64_t)k * b_kstep;
+#pragma unroll
                         for (int mt = 0; mt < kMT; mt++) {
-                            if (C.S2 + (int64_t)mt * kM >= G.b2) break;
-                            const unsigned aoff = 2u * k * lbo_a + arow + (unsigned)(mt * kM * 16);
-                            const unsigned d = tmem + (unsigned)(((mt * 2 + b) * T.P + ilo) * kN);
-                            const unsigned acc = (j2 == 0 && k == 0) ? 0u : 1u;   // fresh partial per input plane
-                            const uint64_t ad_hi = sdesc(a_hi + aoff, lbo_a, 128);
-                            if (KIND == CDV_MODE_SPLIT_BF16X3) {
-                                // hi*hi and hi*lo share A: the second reuses it from the collector buffer
-                                mma_bf16_fill(d, ad_hi, bd_hi, idesc, acc);
-                                mma_bf16_lastuse(d, ad_hi, bd_lo, idesc, 1u);
-                                mma<KIND>(d, sdesc(a_lo + aoff, lbo_a, 128), bd_hi, idesc, 1u);
-                            } else {
-                                mma<KIND>(d, ad_hi, bd_hi, idesc, acc);
-                            }
+                            if (mt >= nmt) break;
+                            // M tile mt: rows 128 mt.. of the staged plane, its own partial columns
+                            const uint64_t am = ka + (uint64_t)(mt * kM);
+                            mma_step<KIND>(d + (unsigned)(mt * 2 * T.P * kN), ah + am, al + am, bh + kb, bl + kb, idesc,
+                                           acc);
                         }
+                        acc = 1u;
                     }
-                    mma_commit(B_EMPTY(bs));
+                    mma_commit_elect(B_EMPTY(bs));
                     if (++bs == T.ns) { bs = 0; bph ^= 1; }
                 }
                 if (!ok) break;
-                mma_commit(A_EMPTY(ab));
-                mma_commit(ACC_FULL(b));
+                mma_commit_elect(A_EMPTY(ab));
+                mma_commit_elect(ACC_FULL(b));
             }
         }
-        if (!ok) fail();
-        mma_commit(DRAIN);                                        // completes when every issued MMA has
-        if (!mbar_wait(DRAIN, 0)) fail();
+        if (!ok && lane == 0) fail();
+        mma_commit_elect(DRAIN);                                  // completes when every issued MMA has
+        if (!__all_sync(0xffffffffu, mbar_wait(DRAIN, 0)) && lane == 0) fail();
     }
 
     // ---------------- epilogue (warps 2..9): one output row per thread; warpgroup g drains and owns
-    // columns [8g, 8g + 8) of every plane's 16-column accumulator
+    // M tile g (TMEM lanes are reached by warp index mod 4, so each warpgroup covers all 128 rows)
     float loc = 0.f;
     if (warp >= 2) {
-        const int cg = (warp - 2) >> 2;
+        const int mt = (warp - 2) >> 2;
         const int quarter = warp & 3;
         float* stg = reinterpret_cast<float*>(sm + lay.off_stage) + (warp - 2) * 32 * kEC;
         float4* stg4 = reinterpret_cast<float4*>(stg);
@@ -440,11 +451,12 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
         int it = 0;
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
             const TcTile C = TcTile::make(T, tile);
-            float tot[kP][kEC];
+            const bool rows_in = C.S2 + mt * kM < G.b2;               // warp-uniform: M tile holds outputs
+            float tot[kP][kN];
 #pragma unroll
             for (int i = 0; i < kP; i++)
 #pragma unroll
-                for (int c = 0; c < kEC; c++) tot[i][c] = 0.f;
+                for (int c = 0; c < kN; c++) tot[i][c] = 0.f;
             if (run) {
                 for (int64_t u = C.ulo; u <= C.uhi; ++u, ++it) {
                     const int b = it & 1;
@@ -457,14 +469,16 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                     int ilo, ihi;
                     C.plane_range(G, u, ilo, ihi);
+                    if (rows_in) {
 #pragma unroll
-                    for (int i = 0; i < kP; i++) {
-                        if (i < ilo || i > ihi) continue;                 // warp-uniform
-                        float v[kEC];
-                        tmem_ld8(tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)((b * T.P + i) * kN + cg * kEC),
-                                 v);
+                        for (int i = 0; i < kP; i++) {
+                            if (i < ilo || i > ihi) continue;             // warp-uniform
+                            float v[kN];
+                            tmem_ld16(tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)(((mt * 2 + b) * T.P + i) * kN),
+                                      v);
 #pragma unroll
-                        for (int c = 0; c < kEC; c++) tot[i][c] += v[c];
+                            for (int c = 0; c < kN; c++) tot[i][c] += v[c];
+                        }
                     }
                     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
                     __syncwarp();
@@ -475,21 +489,24 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
             // Stores go through a per-warp 32 x 8 staging tile so that each warp instruction touches
             // four output rows of 8 consecutive columns instead of 32 rows of one column.  Row r's two
             // 16-byte halves swap places when bit 2 of r is set: conflict-free on both sides.
+            if (!rows_in) continue;
 #pragma unroll
-            for (int i = 0; i < kP; i++) {
+            for (int q = 0; q < kP * 2; q++) {
+                const int i = q >> 1, h = q & 1;                          // plane, 8-column half
                 const int64_t s1 = C.S1 + i;
                 if (s1 >= G.b1) continue;                                 // warp-uniform
                 __syncwarp();
                 const int sw = (lane >> 2) & 1;
-                stg4[lane * 2 + sw] = make_float4(tot[i][0], tot[i][1], tot[i][2], tot[i][3]);
-                stg4[lane * 2 + (sw ^ 1)] = make_float4(tot[i][4], tot[i][5], tot[i][6], tot[i][7]);
+                stg4[lane * 2 + sw] = make_float4(tot[i][8 * h + 0], tot[i][8 * h + 1], tot[i][8 * h + 2], tot[i][8 * h + 3]);
+                stg4[lane * 2 + (sw ^ 1)] =
+                    make_float4(tot[i][8 * h + 4], tot[i][8 * h + 5], tot[i][8 * h + 6], tot[i][8 * h + 7]);
                 __syncwarp();
 #pragma unroll
                 for (int k = 0; k < 8; k++) {
                     const int r = k * 4 + (lane >> 3), c = lane & 7;
                     const float v = stg[r * 8 + ((((c >> 2) ^ (k & 1))) << 2) + (c & 3)];
-                    const int64_t s2 = C.S2 + quarter * 32 + r;
-                    const int64_t s3 = C.S3 + cg * kEC + c;
+                    const int64_t s2 = C.S2 + mt * kM + quarter * 32 + r;
+                    const int64_t s3 = C.S3 + h * kEC + c;
                     if (s2 >= G.b2 || s3 >= G.b3) continue;
                     const int64_t idx = (s1 * G.b2 + s2) * G.b3 + s3;
                     const int64_t sidx = (s1 * G.b2 + s2) * T.sh_pitch + s3;
