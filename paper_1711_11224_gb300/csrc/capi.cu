@@ -142,6 +142,25 @@ static EncodeTiledFn encode_fn()
 
 static int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// Modelled tensor-pipe cycles of one direction for W output columns per plane (P = 128 / W planes
+// per CTA): per tile and input plane, q2 x (K / 16) MMAs of N = W x (planes reached), each about
+// max(46, N / 2) cycles; K = W + q3 - 1 + e rounded up to 16.
+static double tc_model_cycles(const ConvGeom& g, int W, int e)
+{
+    const int P = 128 / W;
+    const int K = (e + g.q3 + W - 1 + 15) / 16 * 16;
+    double per_tile = 0.0;
+    for (int v = -(g.q1 - 1); v < P; v++) {                       // input plane relative to the tile
+        int nv = 0;
+        for (int i = 0; i < P; i++) nv += (i - v >= 0 && i - v < g.q1) ? 1 : 0;
+        if (nv == 0) continue;
+        const int nn = W * (nv + ((W == 8 && (nv & 1)) ? 1 : 0));
+        per_tile += std::max(46.0, nn / 2.0);
+    }
+    const double tiles = (double)ceil_div(g.b1, P) * ceil_div(g.b2, 256) * ceil_div(g.b3, W);
+    return tiles * per_tile * g.q2 * (K / 16);
+}
+
 // Launch template of the tensor-core engine for one direction.
 static bool tc_config(const cdv_plan* P, const ConvGeom& g, bool fwd, TcArgs& t)
 {
@@ -152,14 +171,15 @@ static bool tc_config(const cdv_plan* P, const ConvGeom& g, bool fwd, TcArgs& t)
     t.nprec = (P->mode == CDV_MODE_SPLIT_BF16X3) ? 2 : 1;
     const int off = g.o3 - (g.q3 - 1);
     t.e = ((off % ept) + ept) % ept;
-    t.K = (t.e + g.q3 + 15 + 15) / 16 * 16;
+    t.W = tc_model_cycles(g, 8, t.e) < tc_model_cycles(g, 16, t.e) ? 8 : 16;
+    t.P = 128 / t.W;
+    t.K = (t.e + g.q3 + t.W - 1 + 15) / 16 * 16;
     t.kchunks = t.K / ept;
-    t.P = 8;
     t.MT = 2;
     t.rows = (128 * t.MT + g.q2 - 1 + 15) / 16 * 16;
     t.tiles1 = ceil_div(g.b1, t.P);
     t.tiles2 = ceil_div(g.b2, 128 * t.MT);
-    t.tiles3 = ceil_div(g.b3, 16);
+    t.tiles3 = ceil_div(g.b3, t.W);
     const int64_t ntiles = (int64_t)t.tiles1 * t.tiles2 * t.tiles3;
     if (ntiles > (1LL << 31) - 1 || t.rows / 2 > 256 || t.K > 256) return false;
     int dev = 0, nsm = 0;
@@ -168,7 +188,7 @@ static bool tc_config(const cdv_plan* P, const ConvGeom& g, bool fwd, TcArgs& t)
         return false;
     t.ntiles = (int)ntiles;
     t.grid = (int)std::min<int64_t>(ntiles, nsm);     // one CTA per SM (about 220 KB of shared memory each)
-    t.tmem_cols = 512;                      // 2 partial buffers x 2 M tiles x 8 planes x 16 columns
+    t.tmem_cols = 512;                      // 2 partial buffers x 2 M tiles x 128 columns
     t.sh_pitch = fwd ? P->pitch_r : P->pitch_x;
     t.err = P->dev_err;
     // deepest template-tile ring that fits: each stage is one template row of one input plane
@@ -218,10 +238,10 @@ static cudaError_t tc_setup(cdv_plan* P)
                 P->rsh[b][p] = P->rsh[b][0];
             }
         }
-    // Toeplitz tiles: per part, q2 x kchunks x (q1*16 rows) x 16 bytes
+    // Toeplitz tiles: per part, q2 x kchunks x (q1*W rows) x 16 bytes
     for (int d = 0; d < 2; d++) {
         TcArgs& t = d ? P->tca : P->tcf;
-        const size_t bytes = (size_t)P->q[1] * t.kchunks * P->q[0] * 16 * 16;
+        const size_t bytes = (size_t)P->q[1] * t.kchunks * P->q[0] * t.W * 16;
         for (int p = 0; p < 2; p++) {
             void* ptr = nullptr;
             if (p < nprec) {
@@ -401,10 +421,10 @@ cdv_status cdv_plan_set_psf(cdv_plan* plan, const float* H, void* stream)
     CDV_CUDA(launch_abs_sum(plan->H, plan->nh, plan->absum, s), "sum |H|");
     if (plan->tc()) {
         const int q3 = plan->q[2];
-        CDV_CUDA(tc_build_btiles(plan->H, plan->q[0], plan->q[1], q3, q3 - 1 + plan->tcf.e, plan->tcf.K,
+        CDV_CUDA(tc_build_btiles(plan->H, plan->q[0], plan->q[1], q3, q3 - 1 + plan->tcf.e, plan->tcf.K, plan->tcf.W,
                                  (int)plan->mode, const_cast<void*>(plan->tcf.bt[0]),
                                  const_cast<void*>(plan->tcf.bt[1]), s), "Toeplitz tiles (forward)");
-        CDV_CUDA(tc_build_btiles(plan->Ht, plan->q[0], plan->q[1], q3, q3 - 1 + plan->tca.e, plan->tca.K,
+        CDV_CUDA(tc_build_btiles(plan->Ht, plan->q[0], plan->q[1], q3, q3 - 1 + plan->tca.e, plan->tca.K, plan->tca.W,
                                  (int)plan->mode, const_cast<void*>(plan->tca.bt[0]),
                                  const_cast<void*>(plan->tca.bt[1]), s), "Toeplitz tiles (adjoint)");
     }

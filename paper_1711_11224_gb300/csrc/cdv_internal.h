@@ -175,7 +175,8 @@ struct TcArgs {
     int e;               // window pad: K index 0 is input column S3 + o3 - (q3-1) - e
     int K;               // window length (elements), multiple of 16
     int kchunks;         // 16-byte chunks along K
-    int P;               // output planes per CTA (N of one MMA = 16 x planes)
+    int W;               // output columns per plane of a tile (8 or 16)
+    int P;               // output planes per CTA (P x W = 128 accumulator columns per M tile)
     int MT;              // 128-row M tiles per CTA
     int rows;            // staged input rows (>= 128*MT + q2 - 1), two TMA boxes of rows/2
     int na, ns;          // input-plane buffers, template-tile stages
@@ -194,8 +195,8 @@ struct TcArgs {
 size_t tc_smem_bytes(const TcArgs& t);
 cudaError_t tc_prepare(int kind);
 cudaError_t tc_launch(const TcArgs& t, const struct CUtensorMap_st* maps, cudaStream_t s);
-cudaError_t tc_build_btiles(const float* w, int q1, int q2, int q3, int D, int K, int kind, void* hi, void* lo,
-                            cudaStream_t s);
+cudaError_t tc_build_btiles(const float* w, int q1, int q2, int q3, int D, int K, int W, int kind, void* hi,
+                            void* lo, cudaStream_t s);
 cudaError_t tc_shadow(const float* src, int64_t a1a2, int64_t a3, int64_t pitch, int kind, void* hi, void* lo,
                       cudaStream_t s);
 

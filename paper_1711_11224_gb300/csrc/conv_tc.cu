@@ -3,33 +3,34 @@
 //
 // For the generic operator out[s] = sum_j w[j] in[s + o - j] (forward:
 // in = X, o = 0, w = H; adjoint: in = R, o = 2p, w = H~), fix the template
-// plane j1 and row j2.  The sum over j3 for 16 consecutive output columns is
-// an input window of K columns times a banded Toeplitz matrix
-// T_{j1,j2}[k, n] = w[j1, j2, n + D - k].  With 128 consecutive output rows
-// as M this is one tcgen05.mma per 16-wide K step:
+// plane j1 and row j2.  The sum over j3 for W (8 or 16) consecutive output
+// columns is an input window of K >= W + q3 - 1 columns times a banded
+// Toeplitz matrix T_{j1,j2}[k, n] = w[j1, j2, n + D - k].  With 128
+// consecutive output rows as M this is one tcgen05.mma per 16-wide K step:
 //     D_{s1}[row, n] += A_{u, j2}[row, k] * T_{s1+o1-u, j2}[k, n]
 // where A_{u, j2} is input plane u read at rows shifted by j2.
 //
 // Shapes chosen for the tensor pipe and for the supply of template tiles:
-//  * N = 16 x (output planes): one input plane u and template row j2 feed the
-//    CTA's P = 8 output planes through Toeplitz tiles of consecutive j1,
-//    which are stored side by side ([j2][K chunk][j1*16 + n]), so one MMA
-//    with N = 16 x (planes in range) <= 128 updates all of them.
-//  * Two M tiles of 128 rows per CTA: every template-tile stage (24 KB for
-//    split-BF16x3 with K = 48) feeds both, which halves the template bytes
-//    streamed from L2 per MMA; the stages were the limiter with one M tile.
-//    Split-BF16x3 issues hi*hi and hi*lo back to back with the A operand kept
-//    in the tensor core's collector buffer, so A is read from shared memory
-//    twice per three products.
+//  * N = W x (output planes): one input plane u and template row j2 feed the
+//    CTA's P = 128 / W output planes through Toeplitz tiles of consecutive
+//    j1, stored side by side ([j2][K chunk][j1*W + n]), so one MMA with
+//    N <= 128 updates all of them.  The tensor pipe executes K / q3 times the
+//    algorithmic work; the host picks W per direction from a cycle model
+//    (W = 8 halves K for templates about 20 wide: K = 32 instead of 48).
+//  * Two M tiles of 128 rows per CTA: every template-tile stage feeds both,
+//    which halves the template bytes streamed from L2 per MMA; the stages
+//    were the limiter with one M tile.  Split-BF16x3 issues hi*hi and hi*lo
+//    back to back with the A operand kept in the tensor core's collector
+//    buffer, so A is read from shared memory twice per three products.
 //  * The row shift j2 is a 16-byte shift of the shared-memory descriptor of
 //    one TMA-staged tile of plane u (K-major, no swizzle: core matrices of
 //    8 rows x 16 bytes, rows 16 bytes apart), so the tile serves all q2 rows.
 //  * Two-level accumulation: the contribution of each input plane goes to a
-//    fresh TMEM partial (two buffers x two M tiles x 8 planes x 16 columns =
-//    all 512 columns), which epilogue warps add into FP32 register totals
-//    while the MMAs of the next plane run.  One TMEM accumulator over all
-//    q1*q2 template rows drifts (the tensor core's FP32 accumulation
-//    truncates): 1e-4 relative for a 31x31x21 template.
+//    fresh TMEM partial (two buffers x two M tiles x 128 columns = all 512
+//    columns), which epilogue warps add into FP32 register totals while the
+//    MMAs of the next plane run.  One TMEM accumulator over all q1*q2
+//    template rows drifts (the tensor core's FP32 accumulation truncates):
+//    1e-4 relative for a 31x31x21 template.
 //  * Persistent CTAs, one per SM, walk the output tiles with their ring and
 //    accumulator counters carried across tiles, so a tile's stores overlap
 //    the next tile's loads and MMAs.
@@ -67,10 +68,9 @@ namespace cdv {
 namespace {
 
 constexpr int kM = 128;
-constexpr int kN = 16;
-constexpr int kP = 8;          // output planes per CTA (N of one MMA up to 128)
+constexpr int kNT = 128;       // accumulator columns per M tile: W output columns x P = 128 / W planes
 constexpr int kMT = 2;         // 128-row M tiles per CTA: each template-tile stage feeds both
-constexpr int kEC = 8;         // accumulator columns per plane drained by one epilogue warpgroup
+constexpr int kEC = 8;         // columns per staged store block
 constexpr int kThreads = 320;
 
 __device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -159,7 +159,21 @@ __device__ __forceinline__ void mbar_arrive(unsigned bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
 }
-__device__ __forceinline__ void tmem_ld16(unsigned taddr, float* v)
+template <int W>
+__device__ __forceinline__ void tmem_ld(unsigned taddr, float* v);
+template <>
+__device__ __forceinline__ void tmem_ld<8>(unsigned taddr, float* v)
+{
+    unsigned r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; i++) v[i] = __uint_as_float(r[i]);
+}
+template <>
+__device__ __forceinline__ void tmem_ld<16>(unsigned taddr, float* v)
 {
     unsigned r[16];
     asm volatile(
@@ -197,7 +211,7 @@ struct TcSmem {
     {
         TcSmem s;
         s.a_bytes = (size_t)t.kchunks * t.rows * 16;              // one part of one input plane
-        s.b_bytes = (size_t)t.kchunks * t.P * kN * 16;           // one part of one ring stage
+        s.b_bytes = (size_t)t.kchunks * t.P * t.W * 16;          // one part of one ring stage
         s.off_b = (size_t)t.na * t.nprec * s.a_bytes;
         s.off_bar = s.off_b + (size_t)t.ns * t.nprec * s.b_bytes;
         s.off_stage = s.off_bar + 512;
@@ -208,7 +222,7 @@ struct TcSmem {
 
 size_t tc_smem_bytes(const TcArgs& t) { return TcSmem::make(t).total + 1024; }
 
-// One output tile: planes [S1, S1 + P), rows [S2, S2 + 128), columns [S3, S3 + 16), and the input
+// One output tile: planes [S1, S1 + P), rows [S2, S2 + 256), columns [S3, S3 + W), and the input
 // planes [ulo, uhi] that reach it.
 struct TcTile {
     int64_t S1, S2, S3, s1_end, ulo, uhi;
@@ -220,10 +234,10 @@ struct TcTile {
         const int t2 = tile % T.tiles2;
         const int t1 = tile / T.tiles2;
         const ConvGeom& G = T.g;
-        c.S1 = (int64_t)t1 * kP;
+        c.S1 = (int64_t)t1 * T.P;
         c.S2 = (int64_t)t2 * kM * kMT;
-        c.S3 = (int64_t)t3 * kN;
-        c.s1_end = min(c.S1 + kP, G.b1);
+        c.S3 = (int64_t)t3 * T.W;
+        c.s1_end = min(c.S1 + T.P, G.b1);
         c.ulo = max((int64_t)0, c.S1 + G.o1 - G.q1 + 1);
         c.uhi = min(G.a1 - 1, c.s1_end - 1 + G.o1);
         return c;
@@ -234,9 +248,24 @@ struct TcTile {
         ilo = (int)max((int64_t)0, u - G.o1 - S1);
         ihi = (int)min(s1_end - 1 - S1, u - G.o1 + G.q1 - 1 - S1);
     }
+    // Planes [lo, hi] the MMA covers for planes [ilo, ihi] in range: N = W x planes must be a multiple
+    // of 16, so with W = 8 an odd count takes one neighbouring plane of the tile (its accumulator
+    // columns are never drained; whatever its template slot holds reaches only those columns, since
+    // column n of the product reads only column n of B).  Returns the padded planes in front (0 or 1).
+    template <int W, int P>
+    __device__ static int padded(int ilo, int ihi, int& lo, int& hi)
+    {
+        lo = ilo;
+        hi = ihi;
+        if (W == 8 && ((ihi - ilo + 1) & 1)) {
+            if (ihi < P - 1) hi = ihi + 1;
+            else { lo = ilo - 1; return 1; }
+        }
+        return 0;
+    }
 };
 
-template <int KIND>
+template <int KIND, int W>
 __global__ void __launch_bounds__(kThreads, 1)
 conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtensorMap mh0,
                const __grid_constant__ CUtensorMap ml0, const __grid_constant__ CUtensorMap mh1,
@@ -244,6 +273,7 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
 {
     constexpr int NPREC = (KIND == CDV_MODE_SPLIT_BF16X3) ? 2 : 1;
     constexpr int EPT = (KIND == CDV_MODE_TF32) ? 4 : 8;       // elements per 16-byte K chunk
+    constexpr int P = kNT / W;                                 // output planes per CTA
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const TcSmem lay = TcSmem::make(T);
@@ -345,19 +375,20 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
                             tma3(dst + (unsigned)((c * T.rows + h * half) * 16), mp, (int)(ws + c * EPT),
                                  (int)(v0 + h * half), (int)u, A_FULL(ab));
                 }
-                int ilo, ihi;
+                int ilo, ihi, lo, hi;
                 C.plane_range(G, u, ilo, ihi);
+                const int front = TcTile::padded<W, P>(ilo, ihi, lo, hi);
                 const int64_t j1lo = C.S1 + ilo + G.o1 - u;
                 const int nv = ihi - ilo + 1;
                 for (int j2 = 0; j2 < G.q2; j2++) {
                     if (!mbar_wait(B_EMPTY(bs), bph ^ 1)) { fail(); break; }
-                    mbar_expect_tx(B_FULL(bs), (unsigned)(NPREC * T.kchunks * nv * kN * 16));
+                    mbar_expect_tx(B_FULL(bs), (unsigned)(NPREC * T.kchunks * nv * W * 16));
                     for (int p = 0; p < NPREC; p++) {
                         const unsigned char* src0 = reinterpret_cast<const unsigned char*>(T.bt[p]);
-                        const unsigned dst = su32(sB + ((size_t)bs * NPREC + p) * lay.b_bytes);
+                        const unsigned dst = su32(sB + ((size_t)bs * NPREC + p) * lay.b_bytes) + (unsigned)(front * W * 16);
                         for (int c = 0; c < T.kchunks; c++) {
-                            const size_t row = ((size_t)j2 * T.kchunks + c) * G.q1 * kN + (size_t)j1lo * kN;
-                            bulk_g2s(dst + (unsigned)(c * T.P * kN * 16), src0 + row * 16, (unsigned)(nv * kN * 16),
+                            const size_t row = ((size_t)j2 * T.kchunks + c) * G.q1 * W + (size_t)j1lo * W;
+                            bulk_g2s(dst + (unsigned)(c * P * W * 16), src0 + row * 16, (unsigned)(nv * W * 16),
                                      B_FULL(bs));
                         }
                     }
@@ -379,7 +410,7 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
         // address plus the start in 16-byte units, which cannot carry out of the 14-bit field for
         // shared-memory addresses below 256 KB.
         const unsigned fmt = (KIND == CDV_MODE_TF32) ? 2u : 1u;
-        const unsigned lbo_a = (unsigned)T.rows * 16, lbo_b = (unsigned)T.P * kN * 16;
+        const unsigned lbo_a = (unsigned)T.rows * 16, lbo_b = (unsigned)(P * W * 16);
         const uint64_t da0 = sdesc(0, lbo_a, 128), db0 = sdesc(0, lbo_b, 128);
         const uint64_t a_kstep = (2u * lbo_a) >> 4, b_kstep = (2u * lbo_b) >> 4;
         const unsigned sA16 = su32(sA) >> 4, sB16 = su32(sB) >> 4;
@@ -397,12 +428,13 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
                 w = w && mbar_wait(A_FULL(ab), (unsigned)((it / T.na) & 1));
                 if (!__all_sync(0xffffffffu, w && !*sflag)) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                int ilo, ihi;
+                int ilo, ihi, lo, hi;
                 C.plane_range(G, u, ilo, ihi);
-                const unsigned n = (unsigned)(kN * (ihi - ilo + 1));
+                TcTile::padded<W, P>(ilo, ihi, lo, hi);
+                const unsigned n = (unsigned)(W * (hi - lo + 1));
                 const unsigned idesc =
                     (1u << 4) | (fmt << 7) | (fmt << 10) | ((n >> 3) << 17) | ((unsigned)(kM >> 4) << 24);
-                const unsigned d = tmem + (unsigned)((b * T.P + ilo) * kN);
+                const unsigned d = tmem + (unsigned)(b * kNT + lo * W);
                 // A of this plane, first row of the shift for j2 = 0 (q2 - 1 rows down)
                 const unsigned a_hi = sA16 + (unsigned)(ab * NPREC) * a_part16 + (unsigned)(G.q2 - 1);
                 const unsigned a_lo = a_hi + (unsigned)(NPREC - 1) * a_part16;
@@ -421,8 +453,7 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
                             if (mt >= nmt) break;
                             // M tile mt: rows 128 mt.. of the staged plane, its own partial columns
                             const uint64_t am = ka + (uint64_t)(mt * kM);
-                            mma_step<KIND>(d + (unsigned)(mt * 2 * T.P * kN), ah + am, al + am, bh + kb, bl + kb, idesc,
-                                           acc);
+                            mma_step<KIND>(d + (unsigned)(mt * 2 * kNT), ah + am, al + am, bh + kb, bl + kb, idesc, acc);
                         }
                         acc = 1u;
                     }
@@ -452,11 +483,11 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
             const TcTile C = TcTile::make(T, tile);
             const bool rows_in = C.S2 + mt * kM < G.b2;               // warp-uniform: M tile holds outputs
-            float tot[kP][kN];
+            float tot[P][W];
 #pragma unroll
-            for (int i = 0; i < kP; i++)
+            for (int i = 0; i < P; i++)
 #pragma unroll
-                for (int c = 0; c < kN; c++) tot[i][c] = 0.f;
+                for (int c = 0; c < W; c++) tot[i][c] = 0.f;
             if (run) {
                 for (int64_t u = C.ulo; u <= C.uhi; ++u, ++it) {
                     const int b = it & 1;
@@ -471,13 +502,12 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
                     C.plane_range(G, u, ilo, ihi);
                     if (rows_in) {
 #pragma unroll
-                        for (int i = 0; i < kP; i++) {
+                        for (int i = 0; i < P; i++) {
                             if (i < ilo || i > ihi) continue;             // warp-uniform
-                            float v[kN];
-                            tmem_ld16(tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)(((mt * 2 + b) * T.P + i) * kN),
-                                      v);
+                            float v[W];
+                            tmem_ld<W>(tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)((mt * 2 + b) * kNT + i * W), v);
 #pragma unroll
-                            for (int c = 0; c < kN; c++) tot[i][c] += v[c];
+                            for (int c = 0; c < W; c++) tot[i][c] += v[c];
                         }
                     }
                     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -491,8 +521,8 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
             // 16-byte halves swap places when bit 2 of r is set: conflict-free on both sides.
             if (!rows_in) continue;
 #pragma unroll
-            for (int q = 0; q < kP * 2; q++) {
-                const int i = q >> 1, h = q & 1;                          // plane, 8-column half
+            for (int q = 0; q < P * (W / kEC); q++) {
+                const int i = q / (W / kEC), h = q % (W / kEC);           // plane, 8-column block
                 const int64_t s1 = C.S1 + i;
                 if (s1 >= G.b1) continue;                                 // warp-uniform
                 __syncwarp();
@@ -572,59 +602,66 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
 
 // ----------------------------------------------------------------- host side
 
-cudaError_t tc_prepare(int kind)
+template <int KIND>
+static cudaError_t tc_prepare_kind()
 {
     const int smax = 220 * 1024;
+    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<KIND, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(conv_tc_kernel<KIND, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    return e;
+}
+
+cudaError_t tc_prepare(int kind)
+{
     switch (kind) {
-    case CDV_MODE_BF16:
-        return cudaFuncSetAttribute(conv_tc_kernel<CDV_MODE_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
-    case CDV_MODE_TF32:
-        return cudaFuncSetAttribute(conv_tc_kernel<CDV_MODE_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
-    case CDV_MODE_SPLIT_BF16X3:
-        return cudaFuncSetAttribute(conv_tc_kernel<CDV_MODE_SPLIT_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    smax);
-    default:
-        return cudaErrorInvalidValue;
+    case CDV_MODE_BF16: return tc_prepare_kind<CDV_MODE_BF16>();
+    case CDV_MODE_TF32: return tc_prepare_kind<CDV_MODE_TF32>();
+    case CDV_MODE_SPLIT_BF16X3: return tc_prepare_kind<CDV_MODE_SPLIT_BF16X3>();
+    default: return cudaErrorInvalidValue;
     }
+}
+
+template <int KIND>
+static void tc_launch_kind(const TcArgs& t, const CUtensorMap* maps, size_t smem, cudaStream_t s)
+{
+    const dim3 grid((unsigned)t.grid);
+    if (t.W == 8)
+        conv_tc_kernel<KIND, 8><<<grid, kThreads, smem, s>>>(t, maps[0], maps[1], maps[2], maps[3]);
+    else
+        conv_tc_kernel<KIND, 16><<<grid, kThreads, smem, s>>>(t, maps[0], maps[1], maps[2], maps[3]);
 }
 
 cudaError_t tc_launch(const TcArgs& t, const CUtensorMap* maps, cudaStream_t s)
 {
+    if ((t.W != 8 && t.W != 16) || t.P * t.W != kNT) return cudaErrorInvalidValue;
     const size_t smem = tc_smem_bytes(t);
-    const dim3 grid((unsigned)t.grid);
     switch (t.kind) {
-    case CDV_MODE_BF16:
-        conv_tc_kernel<CDV_MODE_BF16><<<grid, kThreads, smem, s>>>(t, maps[0], maps[1], maps[2], maps[3]);
-        break;
-    case CDV_MODE_TF32:
-        conv_tc_kernel<CDV_MODE_TF32><<<grid, kThreads, smem, s>>>(t, maps[0], maps[1], maps[2], maps[3]);
-        break;
-    case CDV_MODE_SPLIT_BF16X3:
-        conv_tc_kernel<CDV_MODE_SPLIT_BF16X3><<<grid, kThreads, smem, s>>>(t, maps[0], maps[1], maps[2], maps[3]);
-        break;
-    default:
-        return cudaErrorInvalidValue;
+    case CDV_MODE_BF16: tc_launch_kind<CDV_MODE_BF16>(t, maps, smem, s); break;
+    case CDV_MODE_TF32: tc_launch_kind<CDV_MODE_TF32>(t, maps, smem, s); break;
+    case CDV_MODE_SPLIT_BF16X3: tc_launch_kind<CDV_MODE_SPLIT_BF16X3>(t, maps, smem, s); break;
+    default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
 // Toeplitz tiles T_{j1,j2}[k, n] = w[j1, j2, n + D - k] (zero outside [0, q3)),
 // stored K-major for the MMA with the tiles of all j1 side by side along N:
-// part p, row j2, K chunk c: rows j1*16 + n of 16 bytes (EPT elements of K).
-__global__ void tc_btiles_kernel(const float* w, int q1, int q2, int q3, int D, int K, int kind, unsigned char* hi,
-                                 unsigned char* lo)
+// part p, row j2, K chunk c: rows j1*W + n of 16 bytes (EPT elements of K).
+__global__ void tc_btiles_kernel(const float* w, int q1, int q2, int q3, int D, int K, int W, int kind,
+                                 unsigned char* hi, unsigned char* lo)
 {
     const int ept = (kind == CDV_MODE_TF32) ? 4 : 8;
     const int kch = K / ept;
-    const int64_t total = (int64_t)q1 * q2 * kN * K;
+    const int64_t total = (int64_t)q1 * q2 * W * K;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int k = (int)(i % K);
-        const int n = (int)((i / K) % kN);
-        const int64_t jj = i / ((int64_t)K * kN);                  // j1 * q2 + j2
+        const int n = (int)((i / K) % W);
+        const int64_t jj = i / ((int64_t)K * W);                   // j1 * q2 + j2
         const int j1 = (int)(jj / q2), j2 = (int)(jj % q2);
         const int j3 = n + D - k;
         const float v = (j3 >= 0 && j3 < q3) ? w[jj * q3 + j3] : 0.f;
-        const size_t row = ((size_t)j2 * kch + k / ept) * q1 * kN + (size_t)j1 * kN + n;
+        const size_t row = ((size_t)j2 * kch + k / ept) * q1 * W + (size_t)j1 * W + n;
         const size_t off = row * 16 + (size_t)(k % ept) * (kind == CDV_MODE_TF32 ? 4 : 2);
         if (kind == CDV_MODE_TF32) {
             unsigned t;
@@ -639,12 +676,12 @@ __global__ void tc_btiles_kernel(const float* w, int q1, int q2, int q3, int D, 
     }
 }
 
-cudaError_t tc_build_btiles(const float* w, int q1, int q2, int q3, int D, int K, int kind, void* hi, void* lo,
+cudaError_t tc_build_btiles(const float* w, int q1, int q2, int q3, int D, int K, int W, int kind, void* hi, void* lo,
                             cudaStream_t s)
 {
-    const int64_t total = (int64_t)q1 * q2 * kN * K;
+    const int64_t total = (int64_t)q1 * q2 * W * K;
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
-    tc_btiles_kernel<<<blocks, 256, 0, s>>>(w, q1, q2, q3, D, K, kind, (unsigned char*)hi, (unsigned char*)lo);
+    tc_btiles_kernel<<<blocks, 256, 0, s>>>(w, q1, q2, q3, D, K, W, kind, (unsigned char*)hi, (unsigned char*)lo);
     return cudaGetLastError();
 }
 
