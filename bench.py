@@ -56,15 +56,6 @@ def roofline_peak(mode):
     return "tensor", bf16, "%s BF16 dense peak (cuBLAS burst)" % src
 
 
-# executed tensor-pipe work per algorithmic multiply-add of the tensor-core forms: the Toeplitz
-# window (K of 48 for a 21-wide template) and, for split-BF16x3, three products
-def tc_executed_ratio(mode, q3):
-    ept = 4 if mode == "tf32" else 8
-    e = (ept - (q3 - 1) % ept) % ept
-    K = (e + q3 + 15 + 15) // 16 * 16
-    return (K / q3) * (3 if mode == "split3" else 1)
-
-
 WORKLOADS = {
     "ring3d": "X 512x512x128 filaments (320), H 31x31x21 Gaussian-plus-ring, Y = X (*) H + Poisson noise",
     "fil3d": "X 256x256x64 filaments (40) + background 10, H 15x15x11 Gaussian sigma (1.5,1.5,3), Poisson noise",
@@ -461,10 +452,16 @@ def run_cdv(args):
                        "peak_basis": basis,
                        "achieved_is": "algorithmic flop (2 x prod(m) x prod(2p+1)) / kernel time"}
     if args.mode != "fp32":
-        ratio = tc_executed_ratio(args.mode, P.H.shape[-1])
+        # tensor-pipe work of the dominant kernel as the library counts it (Toeplitz window, ragged
+        # tiles, padded planes, the three products of split-BF16x3)
+        info = pl.describe()
+        d = 0 if dom == "forward" else 1
+        ratio = info["executed_macs"][d] / info["algorithmic_macs"]
         out["roofline"]["executed_tflops"] = achieved * ratio
         out["roofline"]["executed_frac"] = achieved * ratio / peak
         out["roofline"]["executed_per_algorithmic"] = ratio
+        out["roofline"]["tile"] = {"cols_per_plane": info["cols"][d], "K": info["K"][d], "grid": info["grid"][d],
+                                   "tiles": info["tiles"][d]}
     out["clocks"] = clk.summary()
     if rank == 0 and not args.no_forms:
         out["forms"] = forms_report(P, dev, stream)

@@ -99,6 +99,30 @@ cdv_status cdv_plan_set_psf(cdv_plan* plan, const float* H, void* stream);
  * Synchronises the device. */
 cdv_status cdv_plan_lipschitz(const cdv_plan* plan, double* L);
 
+/*
+ * How the plan computes its two convolutions (index 0: forward, Property 1;
+ * index 1: adjoint, Property 2).  The paper has no counterpart: this reports
+ * the engine's tiling so that measured times can be set against the work
+ * the hardware executes.  For the tensor-core modes `cols` is the number of
+ * output columns per plane of one tile (8 or 16), `K` the Toeplitz window
+ * along the contiguous axis and `executed_macs` the multiply-adds the tensor
+ * pipe performs per launch, all products of split-BF16x3 included (padding
+ * of K, of ragged tiles and of odd plane counts counted too).  For the FP32
+ * engine cols = K = 0 and executed_macs = algorithmic_macs.  `grid` is the
+ * number of CTAs of one launch.  Host-only: no device work.
+ */
+typedef struct cdv_plan_info {
+    int32_t mode;
+    int32_t cols[2];
+    int32_t K[2];
+    int32_t grid[2];
+    int64_t tiles[2];
+    double executed_macs[2];
+    double algorithmic_macs;   /* prod(m) * prod(2p+1), the same for both directions */
+} cdv_plan_info;
+
+cdv_status cdv_plan_describe(const cdv_plan* plan, cdv_plan_info* out);
+
 /* Free everything the plan owns.  NULL is accepted. */
 cdv_status cdv_plan_destroy(cdv_plan* plan);
 

@@ -29,7 +29,7 @@ EXPORTS = [
     "cdv_plan_set_psf", "cdv_plan_lipschitz", "cdv_plan_destroy", "cdv_forward", "cdv_adjoint", "cdv_grad_psf",
     "cdv_iter_opts_default", "cdv_iterate", "cdv_iterate_host", "cdv_richardson_lucy", "cdv_plan_sync_status",
     "cdv_grad_psf_static", "cdv_batch_plan_create", "cdv_batch_workspace_size", "cdv_batch_set_psfs",
-    "cdv_batch_iterate", "cdv_batch_destroy",
+    "cdv_batch_iterate", "cdv_batch_destroy", "cdv_plan_describe",
 ]
 
 
@@ -50,6 +50,12 @@ class IterReport(ctypes.Structure):
                 ("trials", ctypes.c_int), ("f0", ctypes.c_double), ("f_final", ctypes.c_double),
                 ("gmac", ctypes.c_double), ("f_hist", ctypes.POINTER(ctypes.c_double)),
                 ("delta_hist", ctypes.POINTER(ctypes.c_double))]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("cols", ctypes.c_int32 * 2), ("K", ctypes.c_int32 * 2),
+                ("grid", ctypes.c_int32 * 2), ("tiles", ctypes.c_int64 * 2), ("executed_macs", ctypes.c_double * 2),
+                ("algorithmic_macs", ctypes.c_double)]
 
 
 _lib = None
@@ -76,6 +82,7 @@ def load(path=LIB_PATH):
     lib.cdv_plan_set_psf.argtypes = [vp, vp, vp]
     lib.cdv_plan_lipschitz.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     lib.cdv_plan_destroy.argtypes = [vp]
+    lib.cdv_plan_describe.argtypes = [vp, ctypes.POINTER(PlanInfo)]
     lib.cdv_forward.argtypes = [vp, i32, vp, vp, vp]
     lib.cdv_adjoint.argtypes = [vp, i32, vp, vp, vp]
     lib.cdv_grad_psf.argtypes = [vp, i32, vp, vp, vp, vp]

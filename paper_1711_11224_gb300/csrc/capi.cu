@@ -443,6 +443,56 @@ cdv_status cdv_plan_lipschitz(const cdv_plan* plan, double* L)
     return CDV_OK;
 }
 
+// Tensor-pipe multiply-adds of one launch of the tensor-core engine: per plane tile, input plane,
+// template row, K step and M tile one MMA of 128 x N x 16 per product, N = W x (planes covered,
+// odd counts padded for W = 8) -- the loops of the kernel, counted on the host.
+static double tc_executed_macs(const TcArgs& t)
+{
+    const ConvGeom& g = t.g;
+    double n_sum = 0.0;
+    for (int t1 = 0; t1 < t.tiles1; t1++) {
+        const int64_t S1 = (int64_t)t1 * t.P, s1_end = std::min<int64_t>(S1 + t.P, g.b1);
+        const int64_t ulo = std::max<int64_t>(0, S1 + g.o1 - g.q1 + 1);
+        const int64_t uhi = std::min<int64_t>(g.a1 - 1, s1_end - 1 + g.o1);
+        for (int64_t u = ulo; u <= uhi; u++) {
+            const int64_t ilo = std::max<int64_t>(0, u - g.o1 - S1);
+            const int64_t ihi = std::min<int64_t>(s1_end - 1 - S1, u - g.o1 + g.q1 - 1 - S1);
+            int64_t nv = ihi - ilo + 1;
+            if (t.W == 8 && (nv & 1)) nv++;
+            n_sum += (double)(t.W * nv);
+        }
+    }
+    double mtiles = 0.0;
+    for (int t2 = 0; t2 < t.tiles2; t2++)
+        mtiles += (double)std::min<int64_t>(t.MT, (g.b2 - (int64_t)t2 * 128 * t.MT + 127) / 128);
+    const double products = (t.nprec == 2) ? 3.0 : 1.0;
+    return n_sum * mtiles * 128.0 * t.K * g.q2 * t.tiles3 * products;
+}
+
+cdv_status cdv_plan_describe(const cdv_plan* plan, cdv_plan_info* out)
+{
+    if (!plan || !out) return fail(CDV_ERR_INVALID_ARG, "NULL argument");
+    *out = cdv_plan_info{};
+    out->mode = (int32_t)plan->mode;
+    out->algorithmic_macs = (double)plan->nx * (double)plan->nh;
+    for (int d = 0; d < 2; d++) {
+        if (plan->mode == CDV_MODE_FP32) {
+            const ConvTile& c = d ? plan->ta : plan->tf;
+            out->grid[d] = c.grid;
+            out->tiles[d] = c.grid;
+            out->executed_macs[d] = out->algorithmic_macs;
+        } else {
+            const TcArgs& t = d ? plan->tca : plan->tcf;
+            out->cols[d] = t.W;
+            out->K[d] = t.K;
+            out->grid[d] = t.grid;
+            out->tiles[d] = t.ntiles;
+            out->executed_macs[d] = tc_executed_macs(t);
+        }
+    }
+    return CDV_OK;
+}
+
 cdv_status cdv_plan_destroy(cdv_plan* plan)
 {
     if (!plan) return CDV_OK;

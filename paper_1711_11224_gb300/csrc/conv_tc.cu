@@ -408,12 +408,14 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
         // ---------------- MMA issuer: the whole warp runs the loop (all values warp-uniform) and one
         // elected lane issues each MMA and commit.  Descriptors are templates with a zero start
         // address plus the start in 16-byte units, which cannot carry out of the 14-bit field for
-        // shared-memory addresses below 256 KB.
+        // CTA-local offsets below 256 KB.
         const unsigned fmt = (KIND == CDV_MODE_TF32) ? 2u : 1u;
         const unsigned lbo_a = (unsigned)T.rows * 16, lbo_b = (unsigned)(P * W * 16);
         const uint64_t da0 = sdesc(0, lbo_a, 128), db0 = sdesc(0, lbo_b, 128);
         const uint64_t a_kstep = (2u * lbo_a) >> 4, b_kstep = (2u * lbo_b) >> 4;
-        const unsigned sA16 = su32(sA) >> 4, sB16 = su32(sB) >> 4;
+        // CTA-local offsets only (as sdesc masks): in a cluster launch the shared-window address also
+        // carries the CTA's rank above bit 18, which must not reach the descriptor
+        const unsigned sA16 = (su32(sA) & 0x3FFFFu) >> 4, sB16 = (su32(sB) & 0x3FFFFu) >> 4;
         const unsigned a_part16 = (unsigned)(lay.a_bytes >> 4), b_part16 = (unsigned)(lay.b_bytes >> 4);
         int bs = 0, it = 0;
         unsigned bph = 0;

@@ -75,6 +75,13 @@ class Plan:
         B.check(self.lib.cdv_plan_workspace_size(self._h, ctypes.byref(v)))
         return int(v.value)
 
+    def describe(self):
+        """Tiling of the two convolutions ([forward, adjoint]) and the MACs the hardware executes."""
+        i = B.PlanInfo()
+        B.check(self.lib.cdv_plan_describe(self._h, ctypes.byref(i)))
+        return {"mode": self.mode, "cols": list(i.cols), "K": list(i.K), "grid": list(i.grid),
+                "tiles": list(i.tiles), "executed_macs": list(i.executed_macs), "algorithmic_macs": i.algorithmic_macs}
+
     # -- template -------------------------------------------------------
     def set_psf(self, H):
         _need(H, self.q, "H")

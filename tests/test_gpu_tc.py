@@ -133,3 +133,39 @@ def test_tc_rl_is_fp32_only():
         pl.set_psf(_dev(np.ones((3, 3, 3)) / 27))
         with pytest.raises(CdvError, match="UNSUPPORTED"):
             pl.richardson_lucy(_dev(np.ones((6, 22, 22))), _dev(np.ones((4, 20, 20))), 2)
+
+
+@pytest.mark.parametrize("mode", ["split3", "bf16", "tf32"])
+def test_tc_describe_counts_the_kernel_loops(mode):
+    """Executed MACs the library reports, recounted here from the tiling it reports."""
+    m, q = (40, 300, 130), (31, 31, 21)
+    p = [(v - 1) // 2 for v in q]
+    with _plan(m, q, mode) as pl:
+        info = pl.describe()
+    ept = 4 if mode == "tf32" else 8
+    nprod = 3 if mode == "split3" else 1
+    assert info["algorithmic_macs"] == float(np.prod(m) * np.prod(q))
+    for d in (0, 1):
+        a = m if d == 0 else tuple(x + 2 * y for x, y in zip(m, p))
+        b = tuple(x + 2 * y for x, y in zip(m, p)) if d == 0 else m
+        o = (0, 0, 0) if d == 0 else tuple(2 * y for y in p)
+        W = info["cols"][d]
+        assert W in (8, 16)
+        e = (o[2] - (q[2] - 1)) % ept
+        K = -(-(e + q[2] + W - 1) // 16) * 16
+        assert info["K"][d] == K
+        P = 128 // W
+        n_sum = 0
+        for S1 in range(0, b[0], P):
+            s1_end = min(S1 + P, b[0])
+            for u in range(max(0, S1 + o[0] - q[0] + 1), min(a[0] - 1, s1_end - 1 + o[0]) + 1):
+                planes = [i for i in range(s1_end - S1) if 0 <= S1 + i + o[0] - u < q[0]]
+                nv = len(planes) + (1 if W == 8 and len(planes) % 2 else 0)
+                n_sum += W * nv
+        mtiles = sum(min(2, -(-(b[1] - S2) // 128)) for S2 in range(0, b[1], 256))
+        tiles3 = -(-b[2] // W)
+        assert info["tiles"][d] == -(-b[0] // P) * -(-b[1] // 256) * tiles3
+        expect = n_sum * mtiles * 128 * K * q[1] * tiles3 * nprod
+        assert info["executed_macs"][d] == pytest.approx(expect, rel=1e-12)
+    # the 21-wide contiguous axis takes 8 columns per plane (K = 32 rather than 48)
+    assert info["cols"] == [8, 8]
