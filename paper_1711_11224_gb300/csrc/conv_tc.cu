@@ -13,8 +13,9 @@
 // Shapes chosen for the tensor pipe and for the supply of template tiles:
 //  * N = W x (output planes): one input plane u and template row j2 feed the
 //    CTA's P = 128 / W output planes through Toeplitz tiles of consecutive
-//    j1, stored side by side ([j2][K chunk][j1*W + n]), so one MMA with
-//    N <= 128 updates all of them.  The tensor pipe executes K / q3 times the
+//    j1, stored side by side in 8-row groups ([j2][j1, n/8][K chunk][n%8]),
+//    so one MMA with N <= 128 updates all of them and one bulk copy per
+//    precision part fetches a stage.  The tensor pipe executes K / q3 times the
 //    algorithmic work; the host picks W per direction from a cycle model
 //    (W = 8 halves K for templates about 20 wide: K = 32 instead of 48).
 //  * Two M tiles of 128 rows per CTA: every template-tile stage feeds both,
@@ -385,12 +386,11 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
                     mbar_expect_tx(B_FULL(bs), (unsigned)(NPREC * T.kchunks * nv * W * 16));
                     for (int p = 0; p < NPREC; p++) {
                         const unsigned char* src0 = reinterpret_cast<const unsigned char*>(T.bt[p]);
-                        const unsigned dst = su32(sB + ((size_t)bs * NPREC + p) * lay.b_bytes) + (unsigned)(front * W * 16);
-                        for (int c = 0; c < T.kchunks; c++) {
-                            const size_t row = ((size_t)j2 * T.kchunks + c) * G.q1 * W + (size_t)j1lo * W;
-                            bulk_g2s(dst + (unsigned)(c * P * W * 16), src0 + row * 16, (unsigned)(nv * W * 16),
-                                     B_FULL(bs));
-                        }
+                        // the tiles of planes j1lo .. j1lo + nv - 1 of template row j2 are one contiguous run
+                        const unsigned dst =
+                            su32(sB + ((size_t)bs * NPREC + p) * lay.b_bytes) + (unsigned)(front * W * T.kchunks * 16);
+                        const size_t grp = ((size_t)j2 * G.q1 + (size_t)j1lo) * (W / 8);
+                        bulk_g2s(dst, src0 + grp * T.kchunks * 128, (unsigned)(nv * W * T.kchunks * 16), B_FULL(bs));
                     }
                     ++nb;
                     if (++bs == T.ns) { bs = 0; bph ^= 1; }
@@ -410,9 +410,11 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
         // address plus the start in 16-byte units, which cannot carry out of the 14-bit field for
         // CTA-local offsets below 256 KB.
         const unsigned fmt = (KIND == CDV_MODE_TF32) ? 2u : 1u;
-        const unsigned lbo_a = (unsigned)T.rows * 16, lbo_b = (unsigned)(P * W * 16);
-        const uint64_t da0 = sdesc(0, lbo_a, 128), db0 = sdesc(0, lbo_b, 128);
-        const uint64_t a_kstep = (2u * lbo_a) >> 4, b_kstep = (2u * lbo_b) >> 4;
+        // A: [K chunk][row][16 B] (K neighbours rows x 16 B apart, 8-row groups 128 B apart);
+        // B: [8-row group][K chunk][8 rows][16 B] (K neighbours 128 B apart, groups kchunks x 128 B)
+        const unsigned lbo_a = (unsigned)T.rows * 16;
+        const uint64_t da0 = sdesc(0, lbo_a, 128), db0 = sdesc(0, 128, (unsigned)T.kchunks * 128);
+        const uint64_t a_kstep = (2u * lbo_a) >> 4, b_kstep = (2u * 128u) >> 4;
         // CTA-local offsets only (as sdesc masks): in a cluster launch the shared-window address also
         // carries the CTA's rank above bit 18, which must not reach the descriptor
         const unsigned sA16 = (su32(sA) & 0x3FFFFu) >> 4, sB16 = (su32(sB) & 0x3FFFFu) >> 4;
@@ -648,8 +650,10 @@ cudaError_t tc_launch(const TcArgs& t, const CUtensorMap* maps, cudaStream_t s)
 }
 
 // Toeplitz tiles T_{j1,j2}[k, n] = w[j1, j2, n + D - k] (zero outside [0, q3)),
-// stored K-major for the MMA with the tiles of all j1 side by side along N:
-// part p, row j2, K chunk c: rows j1*W + n of 16 bytes (EPT elements of K).
+// stored K-major for the MMA with the tiles of all j1 side by side along N, in
+// groups of 8 N rows: part p, row j2, group (j1, n / 8), K chunk c, row n % 8,
+// 16 bytes (EPT elements of K).  The tiles of consecutive j1 for one j2 -- one
+// ring stage -- are then a single contiguous run.
 __global__ void tc_btiles_kernel(const float* w, int q1, int q2, int q3, int D, int K, int W, int kind,
                                  unsigned char* hi, unsigned char* lo)
 {
@@ -663,7 +667,9 @@ __global__ void tc_btiles_kernel(const float* w, int q1, int q2, int q3, int D, 
         const int j1 = (int)(jj / q2), j2 = (int)(jj % q2);
         const int j3 = n + D - k;
         const float v = (j3 >= 0 && j3 < q3) ? w[jj * q3 + j3] : 0.f;
-        const size_t row = ((size_t)j2 * kch + k / ept) * q1 * W + (size_t)j1 * W + n;
+        // group of 8 N rows (j1, n / 8) of template row j2, then K chunk, then the row within the group
+        const size_t grp = ((size_t)j2 * q1 + j1) * (W / 8) + n / 8;
+        const size_t row = (grp * kch + k / ept) * 8 + n % 8;
         const size_t off = row * 16 + (size_t)(k % ept) * (kind == CDV_MODE_TF32 ? 4 : 2);
         if (kind == CDV_MODE_TF32) {
             unsigned t;
