@@ -79,6 +79,9 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip the per-form kernel timings and errors")
     ap.add_argument("--path", default="auto", choices=["auto", "general", "small"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch the iteration's kernels on the stream instead of replaying the CUDA graph "
+                         "(the same kernels; for profilers that do not follow conditional graph nodes)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample-planes", type=int, default=96)
     ap.add_argument("--kernels-only", action="store_true",
@@ -391,7 +394,7 @@ def run_cdv(args):
     # warm-up: at least W steps, and the K-step graph captured outside the clock
     done = 0
     while True:
-        _, rep = pl.iterate(Y, X, K=K, x0="crop", path=args.path)
+        _, rep = pl.iterate(Y, X, K=K, x0="crop", path=args.path, use_graph=not args.no_graph)
         done += K
         if done >= args.warmup:
             break
@@ -403,7 +406,7 @@ def run_cdv(args):
     ev1 = torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
         ev0.record(stream)
-        _, rep = pl.iterate(Y, X, K=K, x0="crop", path=args.path)
+        _, rep = pl.iterate(Y, X, K=K, x0="crop", path=args.path, use_graph=not args.no_graph)
         ev1.record(stream)
         torch.cuda.synchronize()
     if dist:
@@ -418,7 +421,10 @@ def run_cdv(args):
     iters = rep["accepted"] * ws / t
     # one graph: x0, [x0 shadow], state, initial forward, initial decision, then a WHILE loop of trial
     # slots (adjoint, forward, decision: 3 launches per trial), finalize
-    launches = 1 + (0 if args.mode == "fp32" else 1) + 1 + 1 + 1 + 3 * rep["trials"] + 1
+    # (launched on the stream instead, every one of the K + 16 trial slots is launched; spare ones
+    # return at once)
+    slots = rep["trials"] if not args.no_graph else K + 16
+    launches = 1 + (0 if args.mode == "fp32" else 1) + 1 + 1 + 1 + 3 * slots + 1
 
     dtype = {"fp32": "f32", "split3": "bf16x3 (split FP32, FP32 accumulate)", "tf32": "tf32 (FP32 accumulate)",
              "bf16": "bf16 (FP32 accumulate)"}[args.mode]
