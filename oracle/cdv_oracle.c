@@ -213,14 +213,17 @@ static double half_sq_norm(const double* v, int64_t n)
 }
 
 /*
- * Projected gradient for  min f(x) = 1/2 || A x - y ||^2  s.t. x >= 0
- * (Steps 1-3 of the 2-D application, any n):
- *   x_{k+1} = max(x_k - delta_k * (A^T A x_k - A^T y), 0),
- * with delta_k chosen so that f(x_{k+1}) < f(x_k).  The gradient is taken in
- * the residual form A^T (A x - y), equal to Eq. 6 in exact arithmetic.
+ * Projected gradient for  min f(x) = 1/2 || A x - y ||^2 + lambda/2 || x ||^2  s.t. x >= 0
+ * (Steps 1-3 of the 2-D application, any n; lambda = 0 is the paper's objective, lambda > 0 adds
+ * the Tikhonov term the introduction names among the classic regularisers):
+ *   x_{k+1} = max(x_k - delta_k * (A^T A x_k - A^T y + lambda x_k), 0),
+ * with delta_k chosen so that f(x_{k+1}) < f(x_k) + sigma <grad f(x_k), x_{k+1} - x_k>.
+ * sigma = 0 is the paper's decrease condition; sigma in (0, 1) is the Armijo sufficient-decrease
+ * form of it.  The gradient is taken in the residual form A^T (A x - y), equal to Eq. 6 in exact
+ * arithmetic.
  *
  * Step rule (the paper fixes only the decrease condition): every trial starts
- * at delta0; a trial whose f does not decrease is rejected and delta is
+ * at delta0; a trial that fails the condition is rejected and delta is
  * multiplied by beta, at most max_halvings times.  A trial that leaves x
  * unchanged, or an exhausted halving budget, ends the run as converged.
  *
@@ -231,7 +234,7 @@ static double half_sq_norm(const double* v, int64_t n)
  */
 int orc_iterate(int64_t m1, int64_t m2, int64_t m3, int p1, int p2, int p3,
                 const double* Y, const double* H, double* X, int K,
-                double delta0, double beta, int max_halvings,
+                double delta0, double beta, int max_halvings, double lambda, double sigma,
                 double* f_hist, double* delta_hist, int* n_acc, int* n_rej)
 {
     const int64_t n1 = m1 + 2 * p1, n2 = m2 + 2 * p2, n3 = m3 + 2 * p3;
@@ -244,9 +247,10 @@ int orc_iterate(int64_t m1, int64_t m2, int64_t m3, int p1, int p2, int p3,
 
     orc_forward(m1, m2, m3, p1, p2, p3, X, H, r);
     for (int64_t i = 0; i < ny; i++) r[i] -= Y[i];
-    double f = half_sq_norm(r, ny);
+    double f = half_sq_norm(r, ny) + lambda * half_sq_norm(X, nx);
     f_hist[0] = f;
     orc_adjoint(m1, m2, m3, p1, p2, p3, r, H, g);
+    for (int64_t i = 0; i < nx; i++) g[i] += lambda * X[i];       /* grad f(x_k) */
 
     while (acc < K) {
         double delta = delta0;
@@ -254,16 +258,18 @@ int orc_iterate(int64_t m1, int64_t m2, int64_t m3, int p1, int p2, int p3,
         double ft = 0.0;
         for (;;) {
             int moved = 0;
+            double slope = 0.0;                                   /* <grad f(x_k), x_t - x_k> */
             for (int64_t i = 0; i < nx; i++) {
                 const double v = X[i] - delta * g[i];
                 xt[i] = v > 0.0 ? v : 0.0;
                 if (xt[i] != X[i]) moved = 1;
+                slope += g[i] * (xt[i] - X[i]);
             }
             if (!moved) break;
             orc_forward(m1, m2, m3, p1, p2, p3, xt, H, rt);
             for (int64_t i = 0; i < ny; i++) rt[i] -= Y[i];
-            ft = half_sq_norm(rt, ny);
-            if (ft < f) { accepted = 1; break; }
+            ft = half_sq_norm(rt, ny) + lambda * half_sq_norm(xt, nx);
+            if (ft < f + sigma * slope) { accepted = 1; break; }
             rej++;
             if (++halvings > max_halvings) break;
             delta *= beta;
@@ -276,6 +282,7 @@ int orc_iterate(int64_t m1, int64_t m2, int64_t m3, int p1, int p2, int p3,
         acc++;
         f_hist[acc] = f;
         orc_adjoint(m1, m2, m3, p1, p2, p3, r, H, g);
+        for (int64_t i = 0; i < nx; i++) g[i] += lambda * X[i];
     }
     *n_acc = acc;
     *n_rej = rej;

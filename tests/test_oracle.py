@@ -274,3 +274,60 @@ def test_lipschitz_bounds_operator_norm():
     H = synth.ring_psf(q=(7, 7, 5), sigma=(1, 1, 1.5), ring_r=2.5, ring_w=0.7, ring_sz=1.0)
     A = dense_A(H, (4, 5, 3))
     assert np.linalg.norm(A, 2) ** 2 <= oracle.lipschitz(H) * (1 + 1e-12)
+
+
+def _delta_template():
+    H = np.zeros((3, 3))
+    H[1, 1] = 1.0                  # A embeds x in the centre of an (m+2) x (m+2) frame
+    return H
+
+
+def test_tikhonov_identity_template_closed_form():
+    """H = delta, lambda > 0: f = 1/2||x - y_c||^2 + lambda/2 ||x||^2 + const, L = 1 + lambda, and one
+    step of length 1/L from any x_0 lands on the minimiser y_c / (1 + lambda) (y_c > 0)."""
+    rng = np.random.default_rng(11)
+    lam = 0.37
+    Y = rng.random((7, 9)) + 0.5
+    X0 = rng.random((5, 7))
+    out = oracle.iterate(Y, _delta_template(), X0, K=1, tikhonov=lam)
+    yc = Y[1:-1, 1:-1]
+    np.testing.assert_allclose(out["X"], yc / (1 + lam), rtol=1e-14)
+    assert out["delta"][0] == pytest.approx(1 / (1 + lam), rel=1e-15)
+    border = 0.5 * (np.sum(Y ** 2) - np.sum(yc ** 2))
+    f1 = 0.5 * np.sum((yc / (1 + lam) - yc) ** 2) + border + 0.5 * lam * np.sum((yc / (1 + lam)) ** 2)
+    assert out["f"][1] == pytest.approx(f1, rel=1e-13)
+    f0 = 0.5 * np.sum((X0 - yc) ** 2) + border + 0.5 * lam * np.sum(X0 ** 2)
+    assert out["f"][0] == pytest.approx(f0, rel=1e-13)
+
+
+@pytest.mark.parametrize("sigma,delta,rejected", [(0.0, 1.0, 0), (0.4, 1.0, 0), (0.6, 0.5, 1)])
+def test_armijo_identity_template_closed_form(sigma, delta, rejected):
+    """H = delta, x_0 = 0, y_c > 0: the full step d = y_c gives f_t - f = -1/2 ||y_c||^2 against
+    sigma <g, d> = -sigma ||y_c||^2, so it passes for sigma < 1/2; at sigma = 0.6 it is rejected and
+    the half step (f_t - f = -3/8 ||y_c||^2 < -0.3 ||y_c||^2) is taken."""
+    rng = np.random.default_rng(12)
+    Y = rng.random((6, 8)) + 0.5
+    out = oracle.iterate(Y, _delta_template(), np.zeros((4, 6)), K=1, armijo=sigma)
+    assert out["accepted"] == 1 and out["rejected"] == rejected
+    assert out["delta"][0] == delta
+    np.testing.assert_allclose(out["X"], delta * Y[1:-1, 1:-1], rtol=1e-15)
+
+
+def test_tikhonov_matches_nnls_augmented():
+    """With lambda > 0 the problem is NNLS on the stacked system [A; sqrt(lambda) I] x ~ [y; 0]."""
+    from scipy.optimize import nnls
+    rng = np.random.default_rng(13)
+    H = synth.gaussian_psf((3, 3), (0.8, 0.8)).astype(np.float64)
+    Xt = np.maximum(rng.standard_normal((8, 8)), 0)
+    Y = oracle.forward(Xt, H) + 0.05 * rng.standard_normal((10, 10))
+    lam = 0.05
+    A = dense_A(H, (8, 8))
+    As = np.vstack([A, np.sqrt(lam) * np.eye(64)])
+    xs, _ = nnls(As, np.concatenate([Y.ravel(), np.zeros(64)]), maxiter=5000)
+    for sigma in (0.0, 1e-4, 0.3):
+        out = oracle.iterate(Y, H, np.zeros((8, 8)), K=20000, tikhonov=lam, armijo=sigma)
+        f = out["f"]
+        assert np.all(np.diff(f) < 0)
+        fs = 0.5 * np.sum((A @ xs - Y.ravel()) ** 2) + 0.5 * lam * np.sum(xs ** 2)
+        assert f[-1] - fs <= 1e-10 * max(fs, 1.0)
+        np.testing.assert_allclose(out["X"].ravel(), xs, atol=1e-6)
