@@ -184,6 +184,12 @@ typedef struct {
     int use_graph;      /* 1: replay the captured K-step sequence as a CUDA graph (default) */
     int path;           /* cdv_iter_path, default CDV_PATH_AUTO */
     int reserved[3];
+    double tikhonov;    /* lambda >= 0 of the term lambda/2 ||x||^2 added to f, default 0 (the
+                           paper's objective); the introduction names Tikhonov regularisation */
+    double armijo;      /* sigma in [0, 1): a trial is accepted when f(x_t) < f(x_k) +
+                           sigma <grad f(x_k), x_t - x_k>; 0 (default) is the decrease
+                           condition of Step 2.  Nonzero tikhonov or armijo: general path only
+                           (CDV_ERR_UNSUPPORTED on the single-CTA path and the batched solver) */
 } cdv_iter_opts;
 
 /* Which kernels run the iteration. */
@@ -204,7 +210,7 @@ typedef struct {
     int status;         /* cdv_status of the run: CDV_OK, CDV_ERR_NOT_DESCENDING
                            (converged: no decreasing step), CDV_ERR_NONFINITE */
     int trials;         /* forward convolutions run after the initial one */
-    double f0;          /* f(x_0) = 1/2 ||A x_0 - y||^2 */
+    double f0;          /* f(x_0) = 1/2 ||A x_0 - y||^2 (+ lambda/2 ||x_0||^2) */
     double f_final;     /* f at the last accepted iterate */
     double gmac;        /* algorithmic multiply-adds executed, in units of 1e9 */
     double* f_hist;     /* optional host array of K+1: f(x_0), ..., f(x_accepted) */
@@ -216,6 +222,10 @@ typedef struct {
  *   x_{k+1} = max(x_k - delta_k A^T (A x_k - y), 0)
  * (the residual form of Eq. 6), for K accepted steps, with delta_k the first
  * of delta0, delta0*beta, delta0*beta^2, ... that makes f(x_{k+1}) < f(x_k).
+ * With opts->tikhonov = lambda > 0 the objective is 1/2 ||A x - y||^2 +
+ * lambda/2 ||x||^2 and the gradient gains lambda x_k (default delta0 =
+ * 1/((sum |h|)^2 + lambda)); with opts->armijo = sigma > 0 the condition is
+ * f(x_{k+1}) < f(x_k) + sigma <grad f(x_k), x_{k+1} - x_k>.
  * Every decision is taken on the device (FP64 objective), so the whole run is
  * one CUDA-graph replay with no host round trip.
  * Y: m + 2p (device), X: m (device; x_0 in per policy, x_K out).

@@ -70,6 +70,8 @@ struct cdv_plan {
     float* aux = nullptr;
     double* part_f = nullptr;
     double* part_m = nullptr;
+    double* part_a = nullptr;
+    double* part_x = nullptr;
     int nparts = 0;
     IterState* st = nullptr;
     double* f_hist = nullptr;
@@ -92,7 +94,7 @@ struct cdv_plan {
         float* x;
         int K;
         int policy, max_halvings, max_rejects;
-        double delta0, beta;
+        double delta0, beta, tikhonov, armijo;
     } key{};
     bool key_valid = false;
     size_t bytes = 0;
@@ -390,6 +392,8 @@ cdv_status cdv_plan_create(cdv_plan** out, int n, const int64_t* m, const int32_
     if (e == cudaSuccess) e = P->alloc(&P->ydev, P->ny);
     if (e == cudaSuccess) e = P->alloc(&P->part_f, P->nparts);
     if (e == cudaSuccess) e = P->alloc(&P->part_m, P->nparts);
+    if (e == cudaSuccess) e = P->alloc(&P->part_a, P->nparts);
+    if (e == cudaSuccess) e = P->alloc(&P->part_x, P->nparts);
     if (e == cudaSuccess) e = P->alloc(&P->st, 1);
     if (e == cudaSuccess) e = P->alloc(&P->f_hist, kHistCap + 1);
     if (e == cudaSuccess) e = P->alloc(&P->d_hist, kHistCap);
@@ -570,6 +574,8 @@ static IterCtx make_ctx(cdv_plan* P, const float* Y, float* X)
     c.aux = P->aux;
     c.part_f = P->part_f;
     c.part_m = P->part_m;
+    c.part_a = P->part_a;
+    c.part_x = P->part_x;
     c.st = P->st;
     c.f_hist = P->f_hist;
     c.d_hist = P->d_hist;
@@ -610,7 +616,8 @@ static cdv_status run_phase(void* vctx, int phase, bool loop, unsigned long long
             CDV_CUDA(tc_shadow(R.X, P->m[0] * P->m[1], P->m[2], P->pitch_x, (int)P->mode, P->xsh[0][0], P->xsh[0][1], s),
                      "x0 shadow");
         CDV_CUDA(launch_state_init(P->st, R.o.delta0, P->absum, R.o.beta, R.o.max_halvings, R.o.max_rejects, R.K,
-                                   kHistCap, s), "state");
+                                   kHistCap, R.o.tikhonov, R.o.armijo, s), "state");
+        if (R.o.tikhonov != 0.0) CDV_CUDA(launch_sumsq(R.X, P->nx, P->part_x, s), "||x_0||^2");
         if (P->tc()) {
             TcArgs F = P->tcf;
             F.ctx = c;
@@ -704,12 +711,18 @@ cdv_status cdv_iterate(cdv_plan* plan, const float* Y, float* X, int K, const cd
     if (o.max_halvings < 0 || o.max_rejects < 0 || o.max_rejects > 1 << 20)
         return fail(CDV_ERR_INVALID_ARG, "max_halvings/max_rejects");
     if (o.path < CDV_PATH_AUTO || o.path > CDV_PATH_SMALL) return fail(CDV_ERR_INVALID_ARG, "path = %d", o.path);
+    if (!(o.tikhonov >= 0.0 && o.tikhonov < 1e300)) return fail(CDV_ERR_INVALID_ARG, "tikhonov = %g", o.tikhonov);
+    if (!(o.armijo >= 0.0 && o.armijo < 1.0)) return fail(CDV_ERR_INVALID_ARG, "armijo = %g", o.armijo);
+    const bool plain_rule = o.tikhonov == 0.0 && o.armijo == 0.0;
     const double delta0 = o.delta0 > 0.0 ? o.delta0 : 0.0;
     cudaStream_t s = (cudaStream_t)stream;
     const bool small_ok = !plan->tc() && small_supported(plan->m, plan->p);
     if (o.path == CDV_PATH_SMALL && !small_ok)
         return fail(CDV_ERR_UNSUPPORTED, "problem does not fit the single-CTA path (%zu bytes of shared memory)",
                     small_smem_bytes(plan->m, plan->p));
+    if (o.path == CDV_PATH_SMALL && !plain_rule)
+        return fail(CDV_ERR_UNSUPPORTED, "the single-CTA path runs the plain step rule (tikhonov = armijo = 0)");
+    if (!plain_rule && o.path == CDV_PATH_AUTO) o.path = CDV_PATH_GENERAL;
     if (o.path == CDV_PATH_SMALL || (o.path == CDV_PATH_AUTO && small_ok)) {
         SmallRun r{};
         for (int i = 0; i < 3; i++) {
@@ -735,7 +748,7 @@ cdv_status cdv_iterate(cdv_plan* plan, const float* Y, float* X, int K, const cd
         return CDV_OK;
     }
     if (o.use_graph) {
-        cdv_plan::Key k{Y, X, K, o.x0_policy, o.max_halvings, o.max_rejects, delta0, o.beta};
+        cdv_plan::Key k{Y, X, K, o.x0_policy, o.max_halvings, o.max_rejects, delta0, o.beta, o.tikhonov, o.armijo};
         const bool same = plan->key_valid && memcmp(&k, &plan->key, sizeof k) == 0;
         if (!same) {
             if (plan->gexec) cudaGraphExecDestroy(plan->gexec);

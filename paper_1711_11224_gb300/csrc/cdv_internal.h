@@ -32,6 +32,8 @@ struct IterState {
     int max_rejects, K, cur, need_grad;
     int done, status, trials, hist_cap;
     int adj_convs, pad_;
+    double lambda;       // Tikhonov weight: f = 1/2 ||A x - y||^2 + lambda/2 ||x||^2
+    double sigma;        // Armijo factor: accept iff f_t < f_k + sigma <grad f(x_k), x_t - x_k>
 };
 
 struct IterCtx {
@@ -42,6 +44,8 @@ struct IterCtx {
     const float* aux;    // Richardson-Lucy: A^T 1
     double* part_f;      // per-CTA partials of ||r||^2
     double* part_m;      // per-CTA partials of ||x_trial - x||^2
+    double* part_a;      // per-CTA partials of <grad f(x_k), x_trial - x_k> (used when sigma != 0)
+    double* part_x;      // per-CTA partials of ||x_trial||^2 (used when lambda != 0)
     IterState* st;
     double* f_hist;      // hist_cap + 1 entries
     double* d_hist;      // hist_cap entries
@@ -105,7 +109,8 @@ ConvTile conv_fp32_tile_shape(const ConvGeom& g, int nty);
 cudaError_t launch_x0(int policy, float* x, const float* y, int64_t m1, int64_t m2, int64_t m3,
                       int p1, int p2, int p3, cudaStream_t s);
 cudaError_t launch_state_init(IterState* st, double delta0, const double* absum, double beta, int max_halvings,
-                              int max_rejects, int K, int hist_cap, cudaStream_t s);
+                              int max_rejects, int K, int hist_cap, double lambda, double sigma, cudaStream_t s);
+cudaError_t launch_sumsq(const float* x, int64_t n, double* out, cudaStream_t s);
 cudaError_t launch_decide(const IterCtx& c, int nparts_f, int nparts_m, int init, cudaStream_t s);
 cudaError_t launch_decide_loop(const IterCtx& c, int nparts_f, int nparts_m, int init, unsigned long long handle,
                                int max_trials, cudaStream_t s);

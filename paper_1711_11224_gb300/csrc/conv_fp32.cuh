@@ -130,10 +130,15 @@ __device__ __forceinline__ void conv_fp32_body(const ConvLaunch& L, const int nt
     bool do_conv = true;
     int cur = 0;
     double delta = 0.0;
+    float lamf = 0.f;
+    bool want_a = false, want_x = false;          // Armijo slope and ||x_t||^2 partials (adjoint trial)
     if (role == ROLE_FWD_INIT || role == ROLE_FWD_TRIAL || role == ROLE_ADJ_TRIAL) {
         const IterState* st = L.ctx.st;
         if (st->done) return;                                   // uniform: the run has finished
         cur = st->cur;
+        lamf = (float)st->lambda;
+        want_a = role == ROLE_ADJ_TRIAL && st->sigma != 0.0;
+        want_x = role == ROLE_ADJ_TRIAL && st->lambda != 0.0;
         if (role == ROLE_FWD_INIT) {
             in = L.ctx.x[cur];
             out = L.ctx.r[cur];
@@ -256,7 +261,7 @@ __device__ __forceinline__ void conv_fp32_body(const ConvLaunch& L, const int nt
     // Epilogue.  Per-element arithmetic in FP32 (FP64 runs at a small fraction of
     // the FP32 rate on this GPU); each thread's squares are summed in FP32 over
     // its <= 32 outputs and the block and grid sums are FP64.
-    float loc = 0.f;
+    float loc = 0.f, loc_a = 0.f, loc_x = 0.f;
     const bool row_ok = active && s2 < G.b2;
     const float deltaf = (float)delta;
 #pragma unroll
@@ -289,10 +294,13 @@ __device__ __forceinline__ void conv_fp32_body(const ConvLaunch& L, const int nt
                     gg = L.ctx.g[idx];
                 }
                 const float xo = L.ctx.x[cur][idx];
-                const float xn = fmaxf(fmaf(-deltaf, gg, xo), 0.f);
+                const float gt = fmaf(lamf, xo, gg);          // grad f = A^T r + lambda x (lambda = 0: A^T r)
+                const float xn = fmaxf(fmaf(-deltaf, gt, xo), 0.f);
                 L.ctx.x[cur ^ 1][idx] = xn;
                 const float d = xn - xo;
                 loc = fmaf(d, d, loc);
+                loc_a = fmaf(gt, d, loc_a);
+                loc_x = fmaf(xn, xn, loc_x);
                 break;
             }
             case ROLE_RL_RATIO: {
@@ -316,6 +324,16 @@ __device__ __forceinline__ void conv_fp32_body(const ConvLaunch& L, const int nt
         if (tid == 0) {
             double* part = (role == ROLE_ADJ_TRIAL) ? L.ctx.part_m : L.ctx.part_f;
             part[tile] = t;
+        }
+        if (want_a) {                                           // uniform
+            __syncthreads();                                    // s_red is reused
+            const double ta = block_sum_f64((double)loc_a, s_red);
+            if (tid == 0) L.ctx.part_a[tile] = ta;
+        }
+        if (want_x) {
+            __syncthreads();
+            const double tx2 = block_sum_f64((double)loc_x, s_red);
+            if (tid == 0) L.ctx.part_x[tile] = tx2;
         }
     }
 }

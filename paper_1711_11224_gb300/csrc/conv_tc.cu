@@ -284,13 +284,17 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
     const int role = T.role;
     int sel = 0, cur = 0;
     bool do_conv = true;
-    float delta = 0.f;
+    float delta = 0.f, lamf = 0.f;
+    bool want_a = false, want_x = false;      // Armijo slope and ||x_t||^2 partials (adjoint trial)
     float* out = T.out;
     const float* xin = nullptr;
     if (role == ROLE_FWD_INIT || role == ROLE_FWD_TRIAL || role == ROLE_ADJ_TRIAL) {
         const IterState* st = T.ctx.st;
         if (st->done) return;
         cur = st->cur;
+        lamf = (float)st->lambda;
+        want_a = role == ROLE_ADJ_TRIAL && st->sigma != 0.0;
+        want_x = role == ROLE_ADJ_TRIAL && st->lambda != 0.0;
         if (role == ROLE_FWD_INIT) {
             sel = cur;
             out = T.ctx.r[cur];
@@ -476,7 +480,7 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
 
     // ---------------- epilogue (warps 2..9): one output row per thread; warpgroup g drains and owns
     // M tile g (TMEM lanes are reached by warp index mod 4, so each warpgroup covers all 128 rows)
-    float loc = 0.f;
+    float loc = 0.f, loc_a = 0.f, loc_x = 0.f;
     if (warp >= 2) {
         const int mt = (warp - 2) >> 2;
         const int quarter = warp & 3;
@@ -565,11 +569,14 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
                             gg = T.ctx.g[idx];
                         }
                         const float xo = xin[idx];
-                        const float xn = fmaxf(fmaf(-delta, gg, xo), 0.f);
+                        const float gt = fmaf(lamf, xo, gg);          // grad f = A^T r + lambda x
+                        const float xn = fmaxf(fmaf(-delta, gt, xo), 0.f);
                         T.ctx.x[cur ^ 1][idx] = xn;
                         store_shadow<KIND>(T.sh_out_hi[cur ^ 1], T.sh_out_lo[cur ^ 1], sidx, xn);
                         const float d = xn - xo;
                         loc = fmaf(d, d, loc);
+                        loc_a = fmaf(gt, d, loc_a);
+                        loc_x = fmaf(xn, xn, loc_x);
                         break;
                     }
                     default:
@@ -582,20 +589,26 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
     }
 
     // ---------------- block partial of the norm, teardown
-    __shared__ double s_red[kThreads / 32];
+    __shared__ double s_red[3][kThreads / 32];
     if (role == ROLE_FWD_INIT || role == ROLE_FWD_TRIAL || role == ROLE_ADJ_TRIAL) {
-        double v = (double)loc;
+        double v[3] = {(double)loc, (double)loc_a, (double)loc_x};
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) s_red[warp] = v;
+        for (int k = 0; k < 3; k++) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+            if (lane == 0) s_red[k][warp] = v[k];
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (tid == 0 && (role == ROLE_FWD_INIT || role == ROLE_FWD_TRIAL || role == ROLE_ADJ_TRIAL)) {
-        double t = 0.0;
-        for (int i = 0; i < kThreads / 32; i++) t += s_red[i];
+        double t[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < kThreads / 32; i++)
+            for (int k = 0; k < 3; k++) t[k] += s_red[k][i];
         double* part = (role == ROLE_ADJ_TRIAL) ? T.ctx.part_m : T.ctx.part_f;
-        part[blockIdx.x] = t;
+        part[blockIdx.x] = t[0];
+        if (want_a) T.ctx.part_a[blockIdx.x] = t[1];
+        if (want_x) T.ctx.part_x[blockIdx.x] = t[2];
     }
     if (run && warp == 0) {
         __syncwarp();

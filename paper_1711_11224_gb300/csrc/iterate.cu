@@ -3,10 +3,13 @@
 //
 // One step of the run is a fixed three-launch "trial slot":
 //   1. adjoint trial  g = A^T r_k (skipped after a rejected trial, g reused),
-//                     x_t = max(x_k - delta g, 0), partials of ||x_t - x_k||^2
+//                     x_t = max(x_k - delta (g + lambda x_k), 0), partials of
+//                     ||x_t - x_k||^2 (and, when used, of <g + lambda x_k, x_t - x_k>
+//                     and ||x_t||^2)
 //   2. forward trial  r_t = A x_t - y, partials of ||r_t||^2
-//   3. decide         f_t = 1/2 ||r_t||^2 (FP64, fixed-order reduction);
-//                     accept if f_t < f_k (the decrease rule of Step 2),
+//   3. decide         f_t = 1/2 ||r_t||^2 + lambda/2 ||x_t||^2 (FP64, fixed-order
+//                     reductions); accept if f_t < f_k + sigma <grad f(x_k), x_t - x_k>
+//                     (lambda = sigma = 0: the decrease rule of Step 2),
 //                     else delta <- beta * delta and retry from x_k.
 // All decisions live in IterState on the device, so the slots of a whole run
 // can be captured in one CUDA graph and replayed without host round trips.
@@ -46,11 +49,12 @@ cudaError_t launch_x0(int policy, float* x, const float* y, int64_t m1, int64_t 
 }
 
 __device__ void state_init_kernel_body(IterState* st, double delta0, const double* absum, double beta,
-                                       int max_halvings, int max_rejects, int K, int hist_cap)
+                                       int max_halvings, int max_rejects, int K, int hist_cap, double lambda,
+                                       double sigma)
 {
-    if (!(delta0 > 0.0)) {                // default step 1/L, L = (sum |h|)^2 >= ||A||_2^2
+    if (!(delta0 > 0.0)) {                // default step 1/L, L = (sum |h|)^2 + lambda >= ||A||_2^2 + lambda
         const double a = *absum;
-        delta0 = 1.0 / (a * a);
+        delta0 = 1.0 / (a * a + lambda);
     }
     st->f_cur = 0.0;
     st->f_trial = 0.0;
@@ -72,18 +76,41 @@ __device__ void state_init_kernel_body(IterState* st, double delta0, const doubl
     st->hist_cap = hist_cap;
     st->adj_convs = 0;
     st->pad_ = 0;
+    st->lambda = lambda;
+    st->sigma = sigma;
 }
 
 __global__ void state_init_kernel(IterState* st, double delta0, const double* absum, double beta, int max_halvings,
-                                  int max_rejects, int K, int hist_cap)
+                                  int max_rejects, int K, int hist_cap, double lambda, double sigma)
 {
-    state_init_kernel_body(st, delta0, absum, beta, max_halvings, max_rejects, K, hist_cap);
+    state_init_kernel_body(st, delta0, absum, beta, max_halvings, max_rejects, K, hist_cap, lambda, sigma);
 }
 
 cudaError_t launch_state_init(IterState* st, double delta0, const double* absum, double beta, int max_halvings,
-                              int max_rejects, int K, int hist_cap, cudaStream_t s)
+                              int max_rejects, int K, int hist_cap, double lambda, double sigma, cudaStream_t s)
 {
-    state_init_kernel<<<1, 1, 0, s>>>(st, delta0, absum, beta, max_halvings, max_rejects, K, hist_cap);
+    state_init_kernel<<<1, 1, 0, s>>>(st, delta0, absum, beta, max_halvings, max_rejects, K, hist_cap, lambda, sigma);
+    return cudaGetLastError();
+}
+
+// ||x||^2 of the initial iterate in FP64, one block, fixed order (the Tikhonov part of f(x_0)).
+__global__ void __launch_bounds__(512) sumsq_kernel(const float* x, int64_t n, double* out)
+{
+    __shared__ double sh[512];
+    double v = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) v += (double)x[i] * (double)x[i];
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+cudaError_t launch_sumsq(const float* x, int64_t n, double* out, cudaStream_t s)
+{
+    sumsq_kernel<<<1, 512, 0, s>>>(x, n, out);
     return cudaGetLastError();
 }
 
@@ -108,8 +135,11 @@ __device__ void decide_body(const IterCtx& c, int nf, int nm, int init, double* 
 {
     IterState* st = c.st;
     if (st->done) return;
-    const double F = 0.5 * block_reduce_fixed(c.part_f, nf, sh);
+    const double lambda = st->lambda, sigma = st->sigma;
+    double F = 0.5 * block_reduce_fixed(c.part_f, nf, sh);
     const double M = init ? 0.0 : block_reduce_fixed(c.part_m, nm, sh);
+    if (lambda != 0.0) F += 0.5 * lambda * block_reduce_fixed(c.part_x, init ? 1 : nm, sh);
+    const double D = (sigma != 0.0 && !init) ? block_reduce_fixed(c.part_a, nm, sh) : 0.0;
     if (threadIdx.x != 0) return;
     if (init) {
         st->f_cur = F;
@@ -137,7 +167,7 @@ __device__ void decide_body(const IterCtx& c, int nf, int nm, int init, double* 
         st->done = 1;
         return;
     }
-    if (F < st->f_cur) {                  // f(x_{k+1}) < f(x_k): accept
+    if (F < st->f_cur + sigma * D) {      // f(x_{k+1}) < f(x_k) (+ sigma <grad f, x_{k+1} - x_k>): accept
         const int a = st->accepted;
         if (a < st->hist_cap) {
             c.d_hist[a] = st->delta;
@@ -249,7 +279,7 @@ __global__ void batch_state_init_kernel(const BatchVolCtx* v, int count, double 
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
-    state_init_kernel_body(v[i].c.st, delta0, v[i].absum, beta, max_halvings, max_rejects, K, hist_cap);
+    state_init_kernel_body(v[i].c.st, delta0, v[i].absum, beta, max_halvings, max_rejects, K, hist_cap, 0.0, 0.0);
 }
 
 __global__ void __launch_bounds__(512) batch_decide_kernel(const BatchVolCtx* v, int init)

@@ -132,7 +132,10 @@ class Plan:
 
     # -- iteration ------------------------------------------------------
     @staticmethod
-    def opts(x0="given", delta0=None, beta=0.5, max_halvings=20, max_rejects=16, use_graph=True, path="auto"):
+    def opts(x0="given", delta0=None, beta=0.5, max_halvings=20, max_rejects=16, use_graph=True, path="auto",
+             tikhonov=0.0, armijo=0.0):
+        """Options of Steps 1-3; tikhonov adds lambda/2 ||x||^2 to f, armijo is the sufficient-decrease
+        factor sigma (both 0: the paper's objective and decrease rule)."""
         o = B.IterOpts()
         B.load().cdv_iter_opts_default(ctypes.byref(o))
         o.x0_policy = B.X0[x0]
@@ -142,6 +145,8 @@ class Plan:
         o.max_rejects = int(max_rejects)
         o.use_graph = 1 if use_graph else 0
         o.path = B.PATHS[path]
+        o.tikhonov = float(tikhonov)
+        o.armijo = float(armijo)
         return o
 
     def _report(self, K, want):

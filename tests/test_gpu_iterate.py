@@ -189,3 +189,51 @@ def test_resume_equals_uninterrupted_run():
         Xc, rb2 = pl.iterate(Y, _dev(ckpt), K=7, x0="given", path="general")
     np.testing.assert_array_equal(Xa.cpu().numpy(), Xc.cpu().numpy())
     np.testing.assert_array_equal(ra["f"][5:], rb2["f"])
+
+
+@pytest.mark.parametrize("lam,sigma", [(0.05, 0.0), (0.0, 0.3), (0.05, 0.1)])
+def test_tikhonov_armijo_match_oracle(lam, sigma):
+    """The Tikhonov term (gradient + lambda x, f + lambda/2 ||x||^2) and the Armijo condition on the
+    general path (several CTAs, stream and graph launches) against the FP64 oracle."""
+    P = synth.scaled_fil3d((12, 60, 50), (5, 5, 7), K=12)
+    ref = oracle.iterate(P.Y, P.H, oracle.x0_crop(P.Y, P.p), 12, tikhonov=lam, armijo=sigma)
+    for g in (True, False):
+        Xg, rep = _run(P, 12, tikhonov=lam, armijo=sigma, use_graph=g)
+        assert rep["accepted"] == ref["accepted"] == 12 and rep["status"] == "CDV_OK"
+        assert rep["rejected"] == ref["rejected"]
+        np.testing.assert_allclose(rep["delta"], ref["delta"], rtol=1e-12)
+        np.testing.assert_allclose(rep["f"], ref["f"], rtol=1e-5)
+        assert rel_l2(Xg, ref["X"]) <= TOL_ITER
+
+
+@pytest.mark.parametrize("sigma,delta,rejected", [(0.4, 1.0, 0), (0.6, 0.5, 1)])
+def test_armijo_identity_template_closed_form(sigma, delta, rejected):
+    """H = delta, x_0 = 0, y_c > 0: the full step passes the Armijo test for sigma < 1/2 only."""
+    from paper_1711_11224_gb300 import Plan
+    rng = np.random.default_rng(12)
+    Y = (rng.random((6, 8)) + 0.5).astype(np.float32)
+    H = np.zeros((3, 3))
+    H[1, 1] = 1.0
+    with Plan((4, 6), (1, 1)) as pl:
+        pl.set_psf(_dev(H))
+        X, rep = pl.iterate(_dev(Y), _dev(np.zeros((4, 6))), K=1, armijo=sigma, path="general")
+    assert rep["accepted"] == 1 and rep["rejected"] == rejected
+    assert rep["delta"][0] == delta
+    np.testing.assert_array_equal(X.cpu().numpy(), np.float32(delta) * Y[1:-1, 1:-1])
+
+
+def test_step_variants_rejected_where_unsupported():
+    from paper_1711_11224_gb300 import BatchPlan, CdvError, Plan
+    P = synth.blobs2d()
+    with Plan(P.m, P.p) as pl:
+        pl.set_psf(_dev(P.H))
+        with pytest.raises(CdvError, match="UNSUPPORTED"):
+            pl.iterate(_dev(P.Y), K=2, path="small", tikhonov=0.1)
+        X, rep = pl.iterate(_dev(P.Y), K=2, tikhonov=0.1)          # auto: runs on the general path
+        assert rep["accepted"] == 2
+        with pytest.raises(CdvError, match="INVALID_ARG"):
+            pl.iterate(_dev(P.Y), K=2, armijo=1.0)
+    with BatchPlan([P.m], [P.p], autotune=False) as bp:
+        bp.set_psfs([_dev(P.H)])
+        with pytest.raises(CdvError, match="UNSUPPORTED"):
+            bp.iterate([_dev(P.Y)], K=2, armijo=0.1)

@@ -85,6 +85,23 @@ def test_tc_iterate(mode):
     np.testing.assert_allclose(rep["f"], ref["f"], rtol=1e-4 if mode == "split3" else 2e-3)
 
 
+@pytest.mark.parametrize("mode", ["split3", "tf32"])
+def test_tc_tikhonov_armijo(mode):
+    """Tikhonov term and Armijo condition fused into the tensor-core epilogues, against the oracle."""
+    from paper_1711_11224_gb300 import Plan
+    P = synth.scaled_fil3d((20, 140, 50), (7, 9, 11), K=10)
+    lam, sigma = 0.05, 0.1
+    with Plan(P.m, P.p, mode=mode) as pl:
+        pl.set_psf(_dev(P.H))
+        X, rep = pl.iterate(_dev(P.Y), K=10, x0="crop", tikhonov=lam, armijo=sigma)
+        Xg = X.cpu().numpy()
+    ref = oracle.iterate(P.Y, P.H, oracle.x0_crop(P.Y, P.p), 10, tikhonov=lam, armijo=sigma)
+    assert rep["accepted"] == ref["accepted"] == 10 and rep["status"] == "CDV_OK"
+    np.testing.assert_allclose(rep["delta"], ref["delta"], rtol=1e-12)
+    assert rel_l2(Xg, ref["X"]) <= (TOL_ITER if mode == "split3" else 5e-3)
+    np.testing.assert_allclose(rep["f"], ref["f"], rtol=1e-4 if mode == "split3" else 2e-3)
+
+
 def test_tc_iterate_many_tiles():
     """More output tiles than SMs, so each persistent CTA carries its rings across tiles."""
     from paper_1711_11224_gb300 import Plan
