@@ -71,7 +71,7 @@ def _load():
             lib.orc_adjoint_points.argtypes = dims + [dp, dp, i64, ip, dp]
             lib.orc_grad_psf.argtypes = [i64] + dims + [dp, dp, dp]
             lib.orc_iterate.argtypes = dims + [dp, dp, dp, i32, ctypes.c_double, ctypes.c_double, i32,
-                                               ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_double, i32,
                                                dp, dp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
             lib.orc_iterate.restype = i32
             lib.orc_richardson_lucy.argtypes = dims + [dp, dp, dp, i32]
@@ -205,12 +205,13 @@ def gradient_eq6(X, H, Y):
     return lit, res
 
 
-def iterate(Y, H, X0, K, delta0=None, beta=0.5, max_halvings=20, tikhonov=0.0, armijo=0.0):
+def iterate(Y, H, X0, K, delta0=None, beta=0.5, max_halvings=20, tikhonov=0.0, armijo=0.0, bb=False):
     """Projected gradient (Steps 1-3) from X0 for K accepted steps.
 
     Objective 1/2 ||A x - y||^2 + tikhonov/2 ||x||^2 (tikhonov = 0: the paper's NNLS objective);
     a trial is accepted when f drops below f(x_k) + armijo <grad f(x_k), x_t - x_k> (armijo = 0:
-    the decrease condition of Step 2).  The default step is 1/L with L = (sum |h|)^2 + tikhonov.
+    the decrease condition of Step 2).  The default step is 1/L with L = (sum |h|)^2 + tikhonov;
+    bb = True starts each step from a Barzilai-Borwein length lagged by one step (see cdv_oracle.c).
     Returns dict(X, f, delta, accepted, rejected, status) with f of length
     accepted + 1 (f[0] = f(X0)) and status 0 (K steps) or 1 (converged).
     """
@@ -223,7 +224,7 @@ def iterate(Y, H, X0, K, delta0=None, beta=0.5, max_halvings=20, tikhonov=0.0, a
     dl = np.zeros(max(K, 1))
     na, nr = ctypes.c_int(0), ctypes.c_int(0)
     st = _load().orc_iterate(*_dims(X.shape, p), _ptr(Y), _ptr(H), _ptr(X), int(K),
-                             float(delta0), float(beta), int(max_halvings), float(tikhonov), float(armijo),
+                             float(delta0), float(beta), int(max_halvings), float(tikhonov), float(armijo), int(bool(bb)),
                              _ptr(f), _ptr(dl), ctypes.byref(na), ctypes.byref(nr))
     a = na.value
     return {"X": X, "f": f[:a + 1], "delta": dl[:a], "accepted": a, "rejected": nr.value, "status": int(st)}

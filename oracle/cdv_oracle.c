@@ -222,10 +222,14 @@ static double half_sq_norm(const double* v, int64_t n)
  * form of it.  The gradient is taken in the residual form A^T (A x - y), equal to Eq. 6 in exact
  * arithmetic.
  *
- * Step rule (the paper fixes only the decrease condition): every trial starts
- * at delta0; a trial that fails the condition is rejected and delta is
- * multiplied by beta, at most max_halvings times.  A trial that leaves x
- * unchanged, or an exhausted halving budget, ends the run as converged.
+ * Step rule (the paper fixes only the decrease condition): every step's first
+ * trial uses delta0 (bb = 0), or (bb = 1) a Barzilai-Borwein length lagged by
+ * one step: delta_k = <s, s> / <s, v> with s = x_{k-1} - x_{k-2} and
+ * v = grad f(x_{k-1}) - grad f(x_{k-2}) for k >= 2 (delta0 for k < 2, and when
+ * <s, v> <= 0), clamped to [delta0, 2^20 delta0].  A trial that fails the
+ * condition is rejected and delta is multiplied by beta, at most max_halvings
+ * times.  A trial that leaves x unchanged, or an exhausted halving budget,
+ * ends the run as converged.
  *
  * X holds x_0 on entry and the last accepted iterate on return.
  * f_hist[0..n_acc] receives f(x_0), f(x_1), ...; delta_hist[0..n_acc-1] the
@@ -234,7 +238,7 @@ static double half_sq_norm(const double* v, int64_t n)
  */
 int orc_iterate(int64_t m1, int64_t m2, int64_t m3, int p1, int p2, int p3,
                 const double* Y, const double* H, double* X, int K,
-                double delta0, double beta, int max_halvings, double lambda, double sigma,
+                double delta0, double beta, int max_halvings, double lambda, double sigma, int bb,
                 double* f_hist, double* delta_hist, int* n_acc, int* n_rej)
 {
     const int64_t n1 = m1 + 2 * p1, n2 = m2 + 2 * p2, n3 = m3 + 2 * p3;
@@ -243,7 +247,10 @@ int orc_iterate(int64_t m1, int64_t m2, int64_t m3, int p1, int p2, int p3,
     double* rt = (double*)malloc(sizeof(double) * (size_t)ny);
     double* g = (double*)malloc(sizeof(double) * (size_t)nx);
     double* xt = (double*)malloc(sizeof(double) * (size_t)nx);
+    double* xp = (double*)malloc(sizeof(double) * (size_t)nx);   /* x_{k-1} */
+    double* gp = (double*)malloc(sizeof(double) * (size_t)nx);   /* grad f(x_{k-1}) */
     int status = 0, acc = 0, rej = 0;
+    double bb_delta = delta0;                                     /* first trial of the next step */
 
     orc_forward(m1, m2, m3, p1, p2, p3, X, H, r);
     for (int64_t i = 0; i < ny; i++) r[i] -= Y[i];
@@ -253,7 +260,7 @@ int orc_iterate(int64_t m1, int64_t m2, int64_t m3, int p1, int p2, int p3,
     for (int64_t i = 0; i < nx; i++) g[i] += lambda * X[i];       /* grad f(x_k) */
 
     while (acc < K) {
-        double delta = delta0;
+        double delta = bb ? bb_delta : delta0;
         int halvings = 0, accepted = 0;
         double ft = 0.0;
         for (;;) {
@@ -275,6 +282,24 @@ int orc_iterate(int64_t m1, int64_t m2, int64_t m3, int p1, int p2, int p3,
             delta *= beta;
         }
         if (!accepted) { status = 1; break; }
+        if (bb) {
+            /* the length of the step after next: s = x_k - x_{k-1}, v = grad f(x_k) - grad f(x_{k-1}),
+               formed when grad f(x_k) is, i.e. lagged by one step */
+            if (acc >= 1) {
+                double ss = 0.0, sv = 0.0;
+                for (int64_t i = 0; i < nx; i++) {
+                    const double si = X[i] - xp[i];
+                    ss += si * si;
+                    sv += si * (g[i] - gp[i]);
+                }
+                double d = sv > 0.0 ? ss / sv : delta0 * 1048576.0;
+                if (d < delta0) d = delta0;
+                if (d > delta0 * 1048576.0) d = delta0 * 1048576.0;
+                bb_delta = d;
+            }
+            memcpy(xp, X, sizeof(double) * (size_t)nx);
+            memcpy(gp, g, sizeof(double) * (size_t)nx);
+        }
         memcpy(X, xt, sizeof(double) * (size_t)nx);
         double* tmp = r; r = rt; rt = tmp;
         f = ft;
@@ -286,7 +311,7 @@ int orc_iterate(int64_t m1, int64_t m2, int64_t m3, int p1, int p2, int p3,
     }
     *n_acc = acc;
     *n_rej = rej;
-    free(r); free(rt); free(g); free(xt);
+    free(r); free(rt); free(g); free(xt); free(xp); free(gp);
     return status;
 }
 

@@ -331,3 +331,42 @@ def test_tikhonov_matches_nnls_augmented():
         fs = 0.5 * np.sum((A @ xs - Y.ravel()) ** 2) + 0.5 * lam * np.sum(xs ** 2)
         assert f[-1] - fs <= 1e-10 * max(fs, 1.0)
         np.testing.assert_allclose(out["X"].ravel(), xs, atol=1e-6)
+
+
+def test_bb_reduces_to_fixed_step_when_hessian_is_scalar():
+    """A = c I (template c * delta): grad f(x) - grad f(x') = c^2 (x - x'), so every Barzilai-Borwein
+    length equals 1/c^2 = 1/L and the run is the fixed-step run."""
+    rng = np.random.default_rng(14)
+    H = np.zeros((3, 3, 3))
+    H[1, 1, 1] = 1.7
+    Y = rng.standard_normal((6, 7, 8))
+    X0 = rng.random((4, 5, 6))
+    a = oracle.iterate(Y, H, X0, K=6)
+    b = oracle.iterate(Y, H, X0, K=6, bb=True)
+    np.testing.assert_allclose(b["delta"], a["delta"], rtol=1e-12)
+    np.testing.assert_allclose(b["X"], a["X"], rtol=1e-12, atol=1e-14)
+
+
+def test_bb_converges_to_nnls_in_fewer_steps():
+    """The Barzilai-Borwein run reaches the NNLS optimum (same fixed point, monotone f) in far fewer
+    accepted steps than the fixed step 1/L on an ill-conditioned blur."""
+    from scipy.optimize import nnls
+    rng = np.random.default_rng(15)
+    H = synth.gaussian_psf((5, 5), (1.2, 1.2)).astype(np.float64)
+    Xt = np.maximum(rng.standard_normal((10, 10)), 0)
+    Y = oracle.forward(Xt, H) + 0.02 * rng.standard_normal((14, 14))
+    A = dense_A(H, (10, 10))
+    xs, _ = nnls(A, Y.ravel(), maxiter=10000)
+    fs = 0.5 * np.sum((A @ xs - Y.ravel()) ** 2)
+
+    def steps_to(out, tol):
+        hit = np.nonzero(out["f"] - fs <= tol * fs)[0]
+        return int(hit[0]) if hit.size else None
+
+    plain = oracle.iterate(Y, H, np.zeros((10, 10)), K=4000)
+    bb = oracle.iterate(Y, H, np.zeros((10, 10)), K=4000, bb=True)
+    assert np.all(np.diff(bb["f"]) < 0)
+    nb, npl = steps_to(bb, 1e-6), steps_to(plain, 1e-6)
+    assert nb is not None and (npl is None or nb * 3 < npl)
+    assert np.max(bb["delta"]) > oracle.lipschitz(H) ** -1 * 2       # longer steps than 1/L are taken
+    np.testing.assert_allclose(bb["X"].ravel(), xs, atol=1e-4)
