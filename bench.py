@@ -187,7 +187,7 @@ class Clocks:
 # ---------------------------------------------------------------- GPU arm
 def kernel_hash(mode):
     h = hashlib.sha256()
-    for f in (("conv_fp32.cuh",) if mode == "fp32" else ("conv_tc.cu",)):
+    for f in (("conv_fp32.cuh",) if mode == "fp32" else ("conv_tc.cuh", "conv_tc.cu")):
         h.update(open(os.path.join(ROOT, "paper_1711_11224_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

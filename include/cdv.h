@@ -183,13 +183,18 @@ typedef struct {
     int max_rejects;    /* rejected trials allowed in the whole run, default 16 */
     int use_graph;      /* 1: replay the captured K-step sequence as a CUDA graph (default) */
     int path;           /* cdv_iter_path, default CDV_PATH_AUTO */
-    int reserved[3];
+    int bb;             /* 1: each step's first trial uses a Barzilai-Borwein length lagged by one
+                           step, <s,s>/<s,v> with s = x_{k-1} - x_{k-2}, v = grad f(x_{k-1}) -
+                           grad f(x_{k-2}) (k >= 2; delta0 before, and when <s,v> <= 0), clamped
+                           to [delta0, 2^20 delta0]; 0 (default): delta0 at every step.  General
+                           path only, like tikhonov and armijo */
+    int reserved[2];
     double tikhonov;    /* lambda >= 0 of the term lambda/2 ||x||^2 added to f, default 0 (the
                            paper's objective); the introduction names Tikhonov regularisation */
     double armijo;      /* sigma in [0, 1): a trial is accepted when f(x_t) < f(x_k) +
                            sigma <grad f(x_k), x_t - x_k>; 0 (default) is the decrease
-                           condition of Step 2.  Nonzero tikhonov or armijo: general path only
-                           (CDV_ERR_UNSUPPORTED on the single-CTA path and the batched solver) */
+                           condition of Step 2.  Nonzero tikhonov or armijo (or bb): general path
+                           only (CDV_ERR_UNSUPPORTED on the single-CTA path and the batched solver) */
 } cdv_iter_opts;
 
 /* Which kernels run the iteration. */

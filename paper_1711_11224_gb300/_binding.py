@@ -42,7 +42,8 @@ class CdvError(RuntimeError):
 class IterOpts(ctypes.Structure):
     _fields_ = [("x0_policy", ctypes.c_int), ("delta0", ctypes.c_double), ("beta", ctypes.c_double),
                 ("max_halvings", ctypes.c_int), ("max_rejects", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("path", ctypes.c_int), ("reserved", ctypes.c_int * 3), ("tikhonov", ctypes.c_double),
+                ("path", ctypes.c_int), ("bb", ctypes.c_int), ("reserved", ctypes.c_int * 2),
+                ("tikhonov", ctypes.c_double),
                 ("armijo", ctypes.c_double)]
 
 

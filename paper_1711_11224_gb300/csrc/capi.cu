@@ -72,6 +72,7 @@ struct cdv_plan {
     double* part_m = nullptr;
     double* part_a = nullptr;
     double* part_x = nullptr;
+    double* part_sy = nullptr;
     int nparts = 0;
     IterState* st = nullptr;
     double* f_hist = nullptr;
@@ -95,6 +96,7 @@ struct cdv_plan {
         int K;
         int policy, max_halvings, max_rejects;
         double delta0, beta, tikhonov, armijo;
+        int bb, pad_;
     } key{};
     bool key_valid = false;
     size_t bytes = 0;
@@ -394,6 +396,7 @@ cdv_status cdv_plan_create(cdv_plan** out, int n, const int64_t* m, const int32_
     if (e == cudaSuccess) e = P->alloc(&P->part_m, P->nparts);
     if (e == cudaSuccess) e = P->alloc(&P->part_a, P->nparts);
     if (e == cudaSuccess) e = P->alloc(&P->part_x, P->nparts);
+    if (e == cudaSuccess) e = P->alloc(&P->part_sy, P->nparts);
     if (e == cudaSuccess) e = P->alloc(&P->st, 1);
     if (e == cudaSuccess) e = P->alloc(&P->f_hist, kHistCap + 1);
     if (e == cudaSuccess) e = P->alloc(&P->d_hist, kHistCap);
@@ -576,6 +579,7 @@ static IterCtx make_ctx(cdv_plan* P, const float* Y, float* X)
     c.part_m = P->part_m;
     c.part_a = P->part_a;
     c.part_x = P->part_x;
+    c.part_sy = P->part_sy;
     c.st = P->st;
     c.f_hist = P->f_hist;
     c.d_hist = P->d_hist;
@@ -616,7 +620,7 @@ static cdv_status run_phase(void* vctx, int phase, bool loop, unsigned long long
             CDV_CUDA(tc_shadow(R.X, P->m[0] * P->m[1], P->m[2], P->pitch_x, (int)P->mode, P->xsh[0][0], P->xsh[0][1], s),
                      "x0 shadow");
         CDV_CUDA(launch_state_init(P->st, R.o.delta0, P->absum, R.o.beta, R.o.max_halvings, R.o.max_rejects, R.K,
-                                   kHistCap, R.o.tikhonov, R.o.armijo, s), "state");
+                                   kHistCap, R.o.tikhonov, R.o.armijo, R.o.bb, s), "state");
         if (R.o.tikhonov != 0.0) CDV_CUDA(launch_sumsq(R.X, P->nx, P->part_x, s), "||x_0||^2");
         if (P->tc()) {
             TcArgs F = P->tcf;
@@ -640,6 +644,7 @@ static cdv_status run_phase(void* vctx, int phase, bool loop, unsigned long long
             A.ctx = c;
             F.role = ROLE_FWD_TRIAL;
             A.role = ROLE_ADJ_TRIAL;
+            A.var = (R.o.tikhonov != 0.0 || R.o.armijo != 0.0 || R.o.bb != 0) ? 1 : 0;
             CDV_CUDA(tc_launch(A, P->map_r, s), "adjoint trial (tensor cores)");
             CDV_CUDA(tc_launch(F, P->map_x, s), "forward trial (tensor cores)");
         } else {
@@ -713,7 +718,8 @@ cdv_status cdv_iterate(cdv_plan* plan, const float* Y, float* X, int K, const cd
     if (o.path < CDV_PATH_AUTO || o.path > CDV_PATH_SMALL) return fail(CDV_ERR_INVALID_ARG, "path = %d", o.path);
     if (!(o.tikhonov >= 0.0 && o.tikhonov < 1e300)) return fail(CDV_ERR_INVALID_ARG, "tikhonov = %g", o.tikhonov);
     if (!(o.armijo >= 0.0 && o.armijo < 1.0)) return fail(CDV_ERR_INVALID_ARG, "armijo = %g", o.armijo);
-    const bool plain_rule = o.tikhonov == 0.0 && o.armijo == 0.0;
+    if (o.bb != 0 && o.bb != 1) return fail(CDV_ERR_INVALID_ARG, "bb = %d", o.bb);
+    const bool plain_rule = o.tikhonov == 0.0 && o.armijo == 0.0 && o.bb == 0;
     const double delta0 = o.delta0 > 0.0 ? o.delta0 : 0.0;
     cudaStream_t s = (cudaStream_t)stream;
     const bool small_ok = !plan->tc() && small_supported(plan->m, plan->p);
@@ -721,7 +727,7 @@ cdv_status cdv_iterate(cdv_plan* plan, const float* Y, float* X, int K, const cd
         return fail(CDV_ERR_UNSUPPORTED, "problem does not fit the single-CTA path (%zu bytes of shared memory)",
                     small_smem_bytes(plan->m, plan->p));
     if (o.path == CDV_PATH_SMALL && !plain_rule)
-        return fail(CDV_ERR_UNSUPPORTED, "the single-CTA path runs the plain step rule (tikhonov = armijo = 0)");
+        return fail(CDV_ERR_UNSUPPORTED, "the single-CTA path runs the plain step rule (tikhonov = armijo = bb = 0)");
     if (!plain_rule && o.path == CDV_PATH_AUTO) o.path = CDV_PATH_GENERAL;
     if (o.path == CDV_PATH_SMALL || (o.path == CDV_PATH_AUTO && small_ok)) {
         SmallRun r{};
@@ -748,7 +754,8 @@ cdv_status cdv_iterate(cdv_plan* plan, const float* Y, float* X, int K, const cd
         return CDV_OK;
     }
     if (o.use_graph) {
-        cdv_plan::Key k{Y, X, K, o.x0_policy, o.max_halvings, o.max_rejects, delta0, o.beta, o.tikhonov, o.armijo};
+        cdv_plan::Key k{Y, X, K, o.x0_policy, o.max_halvings, o.max_rejects, delta0, o.beta, o.tikhonov, o.armijo, o.bb,
+                        0};
         const bool same = plan->key_valid && memcmp(&k, &plan->key, sizeof k) == 0;
         if (!same) {
             if (plan->gexec) cudaGraphExecDestroy(plan->gexec);

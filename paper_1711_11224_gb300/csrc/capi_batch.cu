@@ -410,8 +410,8 @@ cdv_status cdv_batch_iterate(cdv_batch* b, const float* const* Y, float* const* 
     if (o.x0_policy < CDV_X0_GIVEN || o.x0_policy > CDV_X0_ZERO || !(o.beta > 0.0 && o.beta < 1.0) ||
         o.max_halvings < 0 || o.max_rejects < 0 || o.max_rejects > (1 << 20))
         return bfail(CDV_ERR_INVALID_ARG, "iteration options");
-    if (o.tikhonov != 0.0 || o.armijo != 0.0)
-        return bfail(CDV_ERR_UNSUPPORTED, "the batched solver runs the plain step rule (tikhonov = armijo = 0)");
+    if (o.tikhonov != 0.0 || o.armijo != 0.0 || o.bb != 0)
+        return bfail(CDV_ERR_UNSUPPORTED, "the batched solver runs the plain step rule (tikhonov = armijo = bb = 0)");
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<const float*> ky(Y, Y + b->count);
     std::vector<float*> kx(X, X + b->count);

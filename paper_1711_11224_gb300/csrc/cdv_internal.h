@@ -34,6 +34,9 @@ struct IterState {
     int adj_convs, pad_;
     double lambda;       // Tikhonov weight: f = 1/2 ||A x - y||^2 + lambda/2 ||x||^2
     double sigma;        // Armijo factor: accept iff f_t < f_k + sigma <grad f(x_k), x_t - x_k>
+    double sy;           // <x_k - x_{k-1}, grad f(x_k) - grad f(x_{k-1})> of the current step (bb)
+    double ss_last;      // ||x_k - x_{k-1}||^2 of the last accepted step (bb)
+    int bb, pad2_;       // bb: Barzilai-Borwein first trials, lagged by one step
 };
 
 struct IterCtx {
@@ -46,6 +49,7 @@ struct IterCtx {
     double* part_m;      // per-CTA partials of ||x_trial - x||^2
     double* part_a;      // per-CTA partials of <grad f(x_k), x_trial - x_k> (used when sigma != 0)
     double* part_x;      // per-CTA partials of ||x_trial||^2 (used when lambda != 0)
+    double* part_sy;     // per-CTA partials of <x_k - x_{k-1}, grad f(x_k) - grad f(x_{k-1})> (bb)
     IterState* st;
     double* f_hist;      // hist_cap + 1 entries
     double* d_hist;      // hist_cap entries
@@ -109,7 +113,8 @@ ConvTile conv_fp32_tile_shape(const ConvGeom& g, int nty);
 cudaError_t launch_x0(int policy, float* x, const float* y, int64_t m1, int64_t m2, int64_t m3,
                       int p1, int p2, int p3, cudaStream_t s);
 cudaError_t launch_state_init(IterState* st, double delta0, const double* absum, double beta, int max_halvings,
-                              int max_rejects, int K, int hist_cap, double lambda, double sigma, cudaStream_t s);
+                              int max_rejects, int K, int hist_cap, double lambda, double sigma, int bb,
+                              cudaStream_t s);
 cudaError_t launch_sumsq(const float* x, int64_t n, double* out, cudaStream_t s);
 cudaError_t launch_decide(const IterCtx& c, int nparts_f, int nparts_m, int init, cudaStream_t s);
 cudaError_t launch_decide_loop(const IterCtx& c, int nparts_f, int nparts_m, int init, unsigned long long handle,
@@ -188,6 +193,7 @@ struct TcArgs {
     int tiles1, tiles2, tiles3;
     int ntiles;          // output tiles (tiles1 x tiles2 x tiles3)
     int grid;            // persistent CTAs (at most one per SM), each walking tiles blockIdx.x + k * grid
+    int var;             // 1: the instantiation with the iteration's step-rule variants (per launch)
     unsigned tmem_cols;
     int64_t sh_pitch;    // row pitch of the output shadows
     float* out;          // ROLE_PLAIN output

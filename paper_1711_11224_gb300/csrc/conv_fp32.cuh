@@ -132,6 +132,7 @@ __device__ __forceinline__ void conv_fp32_body(const ConvLaunch& L, const int nt
     double delta = 0.0;
     float lamf = 0.f;
     bool want_a = false, want_x = false;          // Armijo slope and ||x_t||^2 partials (adjoint trial)
+    bool want_sy = false;                         // <x_k - x_{k-1}, grad f(x_k) - grad f(x_{k-1})> (bb)
     if (role == ROLE_FWD_INIT || role == ROLE_FWD_TRIAL || role == ROLE_ADJ_TRIAL) {
         const IterState* st = L.ctx.st;
         if (st->done) return;                                   // uniform: the run has finished
@@ -139,6 +140,7 @@ __device__ __forceinline__ void conv_fp32_body(const ConvLaunch& L, const int nt
         lamf = (float)st->lambda;
         want_a = role == ROLE_ADJ_TRIAL && st->sigma != 0.0;
         want_x = role == ROLE_ADJ_TRIAL && st->lambda != 0.0;
+        want_sy = role == ROLE_ADJ_TRIAL && st->bb && st->need_grad && st->accepted >= 1;
         if (role == ROLE_FWD_INIT) {
             in = L.ctx.x[cur];
             out = L.ctx.r[cur];
@@ -261,7 +263,7 @@ __device__ __forceinline__ void conv_fp32_body(const ConvLaunch& L, const int nt
     // Epilogue.  Per-element arithmetic in FP32 (FP64 runs at a small fraction of
     // the FP32 rate on this GPU); each thread's squares are summed in FP32 over
     // its <= 32 outputs and the block and grid sums are FP64.
-    float loc = 0.f, loc_a = 0.f, loc_x = 0.f;
+    float loc = 0.f, loc_a = 0.f, loc_x = 0.f, loc_sy = 0.f;
     const bool row_ok = active && s2 < G.b2;
     const float deltaf = (float)delta;
 #pragma unroll
@@ -287,13 +289,17 @@ __device__ __forceinline__ void conv_fp32_body(const ConvLaunch& L, const int nt
             }
             case ROLE_ADJ_TRIAL: {
                 float gg;
+                const float xo = L.ctx.x[cur][idx];
                 if (do_conv) {
                     gg = v;
+                    if (want_sy) {                            // before g and x_{k-1} are overwritten
+                        const float s = xo - L.ctx.x[cur ^ 1][idx];
+                        loc_sy = fmaf(s, fmaf(lamf, s, v - out[idx]), loc_sy);
+                    }
                     out[idx] = gg;
                 } else {
                     gg = L.ctx.g[idx];
                 }
-                const float xo = L.ctx.x[cur][idx];
                 const float gt = fmaf(lamf, xo, gg);          // grad f = A^T r + lambda x (lambda = 0: A^T r)
                 const float xn = fmaxf(fmaf(-deltaf, gt, xo), 0.f);
                 L.ctx.x[cur ^ 1][idx] = xn;
@@ -334,6 +340,11 @@ __device__ __forceinline__ void conv_fp32_body(const ConvLaunch& L, const int nt
             __syncthreads();
             const double tx2 = block_sum_f64((double)loc_x, s_red);
             if (tid == 0) L.ctx.part_x[tile] = tx2;
+        }
+        if (want_sy) {
+            __syncthreads();
+            const double tsy = block_sum_f64((double)loc_sy, s_red);
+            if (tid == 0) L.ctx.part_sy[tile] = tsy;
         }
     }
 }

@@ -50,7 +50,7 @@ cudaError_t launch_x0(int policy, float* x, const float* y, int64_t m1, int64_t 
 
 __device__ void state_init_kernel_body(IterState* st, double delta0, const double* absum, double beta,
                                        int max_halvings, int max_rejects, int K, int hist_cap, double lambda,
-                                       double sigma)
+                                       double sigma, int bb)
 {
     if (!(delta0 > 0.0)) {                // default step 1/L, L = (sum |h|)^2 + lambda >= ||A||_2^2 + lambda
         const double a = *absum;
@@ -78,18 +78,24 @@ __device__ void state_init_kernel_body(IterState* st, double delta0, const doubl
     st->pad_ = 0;
     st->lambda = lambda;
     st->sigma = sigma;
+    st->sy = 0.0;
+    st->ss_last = 0.0;
+    st->bb = bb;
+    st->pad2_ = 0;
 }
 
 __global__ void state_init_kernel(IterState* st, double delta0, const double* absum, double beta, int max_halvings,
-                                  int max_rejects, int K, int hist_cap, double lambda, double sigma)
+                                  int max_rejects, int K, int hist_cap, double lambda, double sigma, int bb)
 {
-    state_init_kernel_body(st, delta0, absum, beta, max_halvings, max_rejects, K, hist_cap, lambda, sigma);
+    state_init_kernel_body(st, delta0, absum, beta, max_halvings, max_rejects, K, hist_cap, lambda, sigma, bb);
 }
 
 cudaError_t launch_state_init(IterState* st, double delta0, const double* absum, double beta, int max_halvings,
-                              int max_rejects, int K, int hist_cap, double lambda, double sigma, cudaStream_t s)
+                              int max_rejects, int K, int hist_cap, double lambda, double sigma, int bb,
+                              cudaStream_t s)
 {
-    state_init_kernel<<<1, 1, 0, s>>>(st, delta0, absum, beta, max_halvings, max_rejects, K, hist_cap, lambda, sigma);
+    state_init_kernel<<<1, 1, 0, s>>>(st, delta0, absum, beta, max_halvings, max_rejects, K, hist_cap, lambda, sigma,
+                                      bb);
     return cudaGetLastError();
 }
 
@@ -140,7 +146,11 @@ __device__ void decide_body(const IterCtx& c, int nf, int nm, int init, double* 
     const double M = init ? 0.0 : block_reduce_fixed(c.part_m, nm, sh);
     if (lambda != 0.0) F += 0.5 * lambda * block_reduce_fixed(c.part_x, init ? 1 : nm, sh);
     const double D = (sigma != 0.0 && !init) ? block_reduce_fixed(c.part_a, nm, sh) : 0.0;
+    // the first trial of a step (a fresh gradient) also brought <x_k - x_{k-1}, grad f(x_k) - grad f(x_{k-1})>
+    const bool new_sy = st->bb && !init && st->need_grad && st->accepted >= 1;
+    const double SY = new_sy ? block_reduce_fixed(c.part_sy, nm, sh) : 0.0;
     if (threadIdx.x != 0) return;
+    if (new_sy) st->sy = SY;
     if (init) {
         st->f_cur = F;
         c.f_hist[0] = F;
@@ -177,7 +187,18 @@ __device__ void decide_body(const IterCtx& c, int nf, int nm, int init, double* 
         st->cur ^= 1;
         st->f_cur = F;
         st->halvings = 0;
-        st->delta = st->delta0;
+        if (st->bb) {                     // next step: <s,s>/<s,v> of (x_k - x_{k-1}, grad f(x_k) - grad f(x_{k-1}))
+            double d = st->delta0;
+            if (a >= 1) {
+                const double dmax = st->delta0 * 1048576.0;
+                d = st->sy > 0.0 ? st->ss_last / st->sy : dmax;
+                d = fmin(fmax(d, st->delta0), dmax);
+            }
+            st->ss_last = M;              // ||x_{k+1} - x_k||^2 for the step after
+            st->delta = d;
+        } else {
+            st->delta = st->delta0;
+        }
         st->need_grad = 1;
         if (st->accepted >= st->K) st->done = 1;
     } else {                              // reject: shorten the step, keep x_k and g_k
@@ -279,7 +300,7 @@ __global__ void batch_state_init_kernel(const BatchVolCtx* v, int count, double 
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
-    state_init_kernel_body(v[i].c.st, delta0, v[i].absum, beta, max_halvings, max_rejects, K, hist_cap, 0.0, 0.0);
+    state_init_kernel_body(v[i].c.st, delta0, v[i].absum, beta, max_halvings, max_rejects, K, hist_cap, 0.0, 0.0, 0);
 }
 
 __global__ void __launch_bounds__(512) batch_decide_kernel(const BatchVolCtx* v, int init)

@@ -133,9 +133,10 @@ class Plan:
     # -- iteration ------------------------------------------------------
     @staticmethod
     def opts(x0="given", delta0=None, beta=0.5, max_halvings=20, max_rejects=16, use_graph=True, path="auto",
-             tikhonov=0.0, armijo=0.0):
+             tikhonov=0.0, armijo=0.0, bb=False):
         """Options of Steps 1-3; tikhonov adds lambda/2 ||x||^2 to f, armijo is the sufficient-decrease
-        factor sigma (both 0: the paper's objective and decrease rule)."""
+        factor sigma, bb starts steps from Barzilai-Borwein lengths (all off: the paper's objective and
+        decrease rule with delta0 at every step)."""
         o = B.IterOpts()
         B.load().cdv_iter_opts_default(ctypes.byref(o))
         o.x0_policy = B.X0[x0]
@@ -147,6 +148,7 @@ class Plan:
         o.path = B.PATHS[path]
         o.tikhonov = float(tikhonov)
         o.armijo = float(armijo)
+        o.bb = 1 if bb else 0
         return o
 
     def _report(self, K, want):

@@ -233,7 +233,25 @@ def test_step_variants_rejected_where_unsupported():
         assert rep["accepted"] == 2
         with pytest.raises(CdvError, match="INVALID_ARG"):
             pl.iterate(_dev(P.Y), K=2, armijo=1.0)
+        with pytest.raises(CdvError, match="UNSUPPORTED"):
+            pl.iterate(_dev(P.Y), K=2, path="small", bb=True)
     with BatchPlan([P.m], [P.p], autotune=False) as bp:
         bp.set_psfs([_dev(P.H)])
         with pytest.raises(CdvError, match="UNSUPPORTED"):
             bp.iterate([_dev(P.Y)], K=2, armijo=0.1)
+
+
+@pytest.mark.parametrize("kw", [{"bb": True}, {"bb": True, "tikhonov": 0.05, "armijo": 1e-4}])
+def test_bb_matches_oracle(kw):
+    """Barzilai-Borwein first trials (lagged by one step) against the FP64 oracle: the same accepted and
+    rejected trials; the lengths <s,s>/<s,v> agree to 2e-3 (v is a difference of FP32 gradients that
+    cancels to about 1e-3 of their size, so its relative error is about 1e-4)."""
+    P = synth.scaled_fil3d((12, 60, 50), (5, 5, 7), K=20)
+    ref = oracle.iterate(P.Y, P.H, oracle.x0_crop(P.Y, P.p), 20, **kw)
+    Xg, rep = _run(P, 20, max_rejects=200, **kw)            # the oracle has no run-wide reject cap
+    assert rep["accepted"] == ref["accepted"] == 20 and rep["status"] == "CDV_OK"
+    assert rep["rejected"] == ref["rejected"] > 0
+    np.testing.assert_allclose(rep["delta"], ref["delta"], rtol=2e-3)
+    assert np.max(ref["delta"]) * (oracle.lipschitz(P.H) + kw.get("tikhonov", 0.0)) > 4   # long steps taken
+    np.testing.assert_allclose(rep["f"], ref["f"], rtol=1e-4)
+    assert rel_l2(Xg, ref["X"]) <= TOL_ITER

@@ -102,6 +102,21 @@ def test_tc_tikhonov_armijo(mode):
     np.testing.assert_allclose(rep["f"], ref["f"], rtol=1e-4 if mode == "split3" else 2e-3)
 
 
+def test_tc_bb():
+    """Barzilai-Borwein first trials with the tensor-core epilogues (split-BF16x3) against the oracle."""
+    from paper_1711_11224_gb300 import Plan
+    P = synth.scaled_fil3d((20, 140, 50), (7, 9, 11), K=20)
+    with Plan(P.m, P.p, mode="split3") as pl:
+        pl.set_psf(_dev(P.H))
+        X, rep = pl.iterate(_dev(P.Y), K=20, x0="crop", bb=True, max_rejects=200)
+        Xg = X.cpu().numpy()
+    ref = oracle.iterate(P.Y, P.H, oracle.x0_crop(P.Y, P.p), 20, bb=True)
+    assert rep["accepted"] == ref["accepted"] == 20 and rep["rejected"] == ref["rejected"]
+    np.testing.assert_allclose(rep["delta"], ref["delta"], rtol=2e-3)
+    assert rel_l2(Xg, ref["X"]) <= TOL_ITER
+    np.testing.assert_allclose(rep["f"], ref["f"], rtol=1e-4)
+
+
 def test_tc_iterate_many_tiles():
     """More output tiles than SMs, so each persistent CTA carries its rings across tiles."""
     from paper_1711_11224_gb300 import Plan
