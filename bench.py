@@ -46,8 +46,17 @@ def measured_peaks():
         return 1900.0, "fallback"
 
 
+def measured_hbm():
+    """Measured HBM copy bandwidth of this machine's GPUs (GB/s), else the recipe's fallback."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
 def roofline_peak(mode):
-    """(bound, peak TFLOP/s, basis) for the convolution kernels of a form."""
+    """(bound, peak TFLOP/s, basis) for the convolution kernels of a form (not the FFT comparator)."""
     if mode == "fp32":
         return "alu", FP32_PEAK_TFLOPS, "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (FFMA)"
     bf16, src = measured_peaks()
@@ -73,9 +82,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cdv", choices=["cdv", "reference"])
     ap.add_argument("--workload", default="ring3d", choices=sorted(WORKLOADS))
-    ap.add_argument("--mode", default="split3", choices=["fp32", "bf16", "tf32", "split3"],
+    ap.add_argument("--mode", default="split3", choices=["fp32", "bf16", "tf32", "split3", "fft"],
                     help="arithmetic of the convolutions (default: split-BF16x3, the fastest form within the FP32 "
-                         "accuracy bar)")
+                         "accuracy bar; fft: the cuFFT comparator, not the paper's method)")
     ap.add_argument("--no-forms", action="store_true", help="skip the per-form kernel timings and errors")
     ap.add_argument("--path", default="auto", choices=["auto", "general", "small"])
     ap.add_argument("--no-e2e", action="store_true")
@@ -224,7 +233,7 @@ def forms_report(P, dev, stream, npts=1000):
     G = torch.empty(P.m, device=dev, dtype=torch.float32)
     flops = 2.0 * float(np.prod(P.m)) * float(P.H.size)
     res = {}
-    for mode in ("fp32", "split3", "tf32", "bf16"):
+    for mode in ("fp32", "split3", "tf32", "bf16", "fft"):
         pl = Plan(P.m, P.p, mode=mode)
         pl.set_psf(torch.from_numpy(P.H).to(dev))
         tf = time_kernel(lambda: pl.forward(X, Y), stream, reps=2)
@@ -233,12 +242,17 @@ def forms_report(P, dev, stream, npts=1000):
         Gh = G.cpu().numpy()
         ef = float(np.linalg.norm(Yh[tuple(si.T)] - yo) / np.linalg.norm(yo))
         ea = float(np.linalg.norm(Gh[tuple(ki.T)] - go) / np.linalg.norm(go))
-        bound, peak, _ = roofline_peak(mode)
         res[mode] = {"forward_ms": tf * 1e3, "adjoint_ms": ta * 1e3,
                      "gmacs_per_conv_pair": flops / (tf + ta) / 1e9,
-                     "forward_frac": flops / tf / 1e12 / peak, "adjoint_frac": flops / ta / 1e12 / peak,
-                     "bound": bound, "rel_l2_forward": ef, "rel_l2_adjoint": ea,
+                     "rel_l2_forward": ef, "rel_l2_adjoint": ea,
                      "sample": "%d sampled outputs per operator vs the FP64 oracle" % npts}
+        if mode == "fft":
+            res[mode]["note"] = ("comparator, not the paper's method: cuFFT transforms of the zero-padded grid; "
+                                 "gmacs_per_conv_pair counts the direct sums it replaces")
+        else:
+            bound, peak, _ = roofline_peak(mode)
+            res[mode].update({"forward_frac": flops / tf / 1e12 / peak, "adjoint_frac": flops / ta / 1e12 / peak,
+                              "bound": bound})
         pl.close()
     return res
 
@@ -424,9 +438,15 @@ def run_cdv(args):
     # (launched on the stream instead, every one of the K + 16 trial slots is launched; spare ones
     # return at once)
     slots = rep["trials"] if not args.no_graph else K + 16
-    launches = 1 + (0 if args.mode == "fp32" else 1) + 1 + 1 + 1 + 3 * slots + 1
+    if args.mode == "fft":
+        # our kernels only (cuFFT's own are not counted): per operator pad, spectrum product, crop with
+        # the fused epilogue
+        launches = 1 + 1 + 3 + 1 + slots * (3 + 3 + 1) + 1
+    else:
+        launches = 1 + (0 if args.mode == "fp32" else 1) + 1 + 1 + 1 + 3 * slots + 1
 
     dtype = {"fp32": "f32", "split3": "bf16x3 (split FP32, FP32 accumulate)", "tf32": "tf32 (FP32 accumulate)",
+             "fft": "f32 (cuFFT comparator)",
              "bf16": "bf16 (FP32 accumulate)"}[args.mode]
     out = {"metric": METRIC, "value": value, "unit": "GMAC/s", "n_gpus": ws, "steps": K, "warmup": args.warmup,
            "ms_per_step": t * 1e3 / max(1, rep["accepted"]), "higher_is_better": True, "scaling": "weak",
@@ -448,16 +468,27 @@ def run_cdv(args):
     flops = 2.0 * nxnh
     dom, tdom = ("forward", tf) if tf >= ta else ("adjoint", ta)
     achieved = flops / tdom / 1e12
-    bound, peak, basis = roofline_peak(args.mode)
-    kname = ("conv_fp32 " if args.mode == "fp32" else "conv_tc<%s> " % args.mode) + dom
-    traffic = traffic_record(args.workload, args.mode, dom)
-    out["roofline"] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                       "frac": achieved / peak, "traffic": traffic, "kernel": kname,
-                       "forward_ms": tf * 1e3, "adjoint_ms": ta * 1e3,
-                       "forward_frac": flops / tf / 1e12 / peak, "adjoint_frac": flops / ta / 1e12 / peak,
-                       "peak_basis": basis,
-                       "achieved_is": "algorithmic flop (2 x prod(m) x prod(2p+1)) / kernel time"}
-    if args.mode != "fp32":
+    if args.mode == "fft":
+        # the comparator streams its input and output through transforms: HBM-bound; algorithmic bytes =
+        # input once + output once of the operator
+        hbm, _ = measured_hbm()
+        byts = 4.0 * (float(np.prod(P.m)) + float(np.prod(P.Y.shape)))
+        out["roofline"] = {"bound": "hbm", "achieved": byts / tdom / 1e9, "peak": hbm, "unit": "GB/s",
+                           "frac": byts / tdom / 1e9 / hbm, "traffic": None, "kernel": "cuFFT convolution " + dom,
+                           "forward_ms": tf * 1e3, "adjoint_ms": ta * 1e3,
+                           "achieved_is": "input + output bytes of the operator / its time (pad, R2C, product, "
+                                          "C2R, crop)"}
+    else:
+        bound, peak, basis = roofline_peak(args.mode)
+        kname = ("conv_fp32 " if args.mode == "fp32" else "conv_tc<%s> " % args.mode) + dom
+        traffic = traffic_record(args.workload, args.mode, dom)
+        out["roofline"] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                           "frac": achieved / peak, "traffic": traffic, "kernel": kname,
+                           "forward_ms": tf * 1e3, "adjoint_ms": ta * 1e3,
+                           "forward_frac": flops / tf / 1e12 / peak, "adjoint_frac": flops / ta / 1e12 / peak,
+                           "peak_basis": basis,
+                           "achieved_is": "algorithmic flop (2 x prod(m) x prod(2p+1)) / kernel time"}
+    if args.mode not in ("fp32", "fft"):
         # tensor-pipe work of the dominant kernel as the library counts it (Toeplitz window, ragged
         # tiles, padded planes, the three products of split-BF16x3)
         info = pl.describe()

@@ -59,7 +59,10 @@ typedef enum {
     CDV_MODE_FP32 = 0,          /* FP32 FMA on CUDA cores */
     CDV_MODE_BF16 = 1,          /* tensor cores, BF16 products, FP32 accumulate */
     CDV_MODE_TF32 = 2,          /* tensor cores, TF32 products, FP32 accumulate */
-    CDV_MODE_SPLIT_BF16X3 = 3   /* tensor cores, x_hi h_hi + x_hi h_lo + x_lo h_hi */
+    CDV_MODE_SPLIT_BF16X3 = 3,  /* tensor cores, x_hi h_hi + x_hi h_lo + x_lo h_hi */
+    CDV_MODE_FFT = 4            /* comparator, not the paper's method: both operators through FP32
+                                   cuFFT transforms of a zero-padded grid (the FFT approach the
+                                   paper's introduction contrasts with); same iteration and reports */
 } cdv_mode;
 
 typedef struct cdv_plan cdv_plan;
@@ -108,7 +111,7 @@ cdv_status cdv_plan_lipschitz(const cdv_plan* plan, double* L);
  * along the contiguous axis and `executed_macs` the multiply-adds the tensor
  * pipe performs per launch, all products of split-BF16x3 included (padding
  * of K, of ragged tiles and of odd plane counts counted too).  For the FP32
- * engine cols = K = 0 and executed_macs = algorithmic_macs.  `grid` is the
+ * engine cols = K = 0 and executed_macs = algorithmic_macs; for CDV_MODE_FFT all are 0.  `grid` is the
  * number of CTAs of one launch.  Host-only: no device work.
  */
 typedef struct cdv_plan_info {

@@ -19,7 +19,7 @@ STATUS = {
     5: "CDV_ERR_CUDA", 6: "CDV_ERR_TIMEOUT", 7: "CDV_ERR_NOT_DESCENDING", 8: "CDV_ERR_NONFINITE",
     9: "CDV_ERR_NO_PSF",
 }
-MODES = {"fp32": 0, "bf16": 1, "tf32": 2, "split3": 3}
+MODES = {"fp32": 0, "bf16": 1, "tf32": 2, "split3": 3, "fft": 4}
 X0 = {"given": 0, "crop": 1, "zero": 2}
 PATHS = {"auto": 0, "general": 1, "small": 2}
 

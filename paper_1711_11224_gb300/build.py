@@ -67,7 +67,7 @@ def build(force=False, verbose=False, jobs=None):
     with ThreadPoolExecutor(jobs) as ex:
         list(ex.map(compile_one, zip(srcs, objs)))
     tmp = LIB + ".%d.tmp" % os.getpid()
-    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
+    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcufft"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))

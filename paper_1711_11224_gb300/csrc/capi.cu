@@ -86,7 +86,9 @@ struct cdv_plan {
     int64_t pitch_x = 0, pitch_r = 0;
     CUtensorMap map_x[4], map_r[4]; // hi0, lo0, hi1, lo1
     int* dev_err = nullptr;
-    bool tc() const { return mode != CDV_MODE_FP32; }
+    bool tc() const { return mode == CDV_MODE_BF16 || mode == CDV_MODE_TF32 || mode == CDV_MODE_SPLIT_BF16X3; }
+    bool fft() const { return mode == CDV_MODE_FFT; }
+    FftPlan fftp{};
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -119,6 +121,7 @@ struct cdv_plan {
         if (graph) cudaGraphDestroy(graph);
         gexec = nullptr;
         graph = nullptr;
+        fft_release(fftp);
         for (void* v : allocs) cudaFree(v);
         allocs.clear();
         if (cap) cudaStreamDestroy(cap);
@@ -309,6 +312,12 @@ void cdv_iter_opts_default(cdv_iter_opts* o)
     o->use_graph = 1;
 }
 
+static void* plan_alloc(void* owner, size_t bytes)
+{
+    unsigned char* v = nullptr;
+    return static_cast<cdv_plan*>(owner)->alloc(&v, bytes) == cudaSuccess ? v : nullptr;
+}
+
 cdv_status cdv_plan_create(cdv_plan** out, int n, const int64_t* m, const int32_t* p, cdv_mode mode, void* stream)
 {
     (void)stream;
@@ -316,7 +325,8 @@ cdv_status cdv_plan_create(cdv_plan** out, int n, const int64_t* m, const int32_
     *out = nullptr;
     if (!m || !p) return fail(CDV_ERR_INVALID_ARG, "m or p is NULL");
     if (n < 1 || n > 3) return fail(CDV_ERR_SHAPE, "n = %d, must be 1, 2 or 3", n);
-    if (mode != CDV_MODE_FP32 && mode != CDV_MODE_BF16 && mode != CDV_MODE_TF32 && mode != CDV_MODE_SPLIT_BF16X3)
+    if (mode != CDV_MODE_FP32 && mode != CDV_MODE_BF16 && mode != CDV_MODE_TF32 && mode != CDV_MODE_SPLIT_BF16X3 &&
+        mode != CDV_MODE_FFT)
         return fail(CDV_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
     for (int i = 0; i < n; i++) {
         if (m[i] < 1) return fail(CDV_ERR_SHAPE, "m[%d] = %lld < 1", i, (long long)m[i]);
@@ -343,7 +353,7 @@ cdv_status cdv_plan_create(cdv_plan** out, int n, const int64_t* m, const int32_
     P->nx = P->m[0] * P->m[1] * P->m[2];
     P->ny = (P->m[0] + 2 * P->p[0]) * (P->m[1] + 2 * P->p[1]) * (P->m[2] + 2 * P->p[2]);
     P->nh = (int64_t)P->q[0] * P->q[1] * P->q[2];
-    if (mode == CDV_MODE_FP32 && !conv_fp32_supported(P->q[2])) {
+    if (mode == CDV_MODE_FP32 && !conv_fp32_supported(P->q[2])) {     // the FFT comparator takes any width
         delete P;
         return fail(CDV_ERR_UNSUPPORTED, "template width %d along the contiguous axis: this build supports odd 1..31",
                     P->q[2]);
@@ -355,7 +365,7 @@ cdv_status cdv_plan_create(cdv_plan** out, int n, const int64_t* m, const int32_
                      2 * P->p[0], 2 * P->p[1], 2 * P->p[2], P->q[0], P->q[1], P->q[2]};
     P->tf = conv_fp32_tile(P->gf);
     P->ta = conv_fp32_tile(P->ga);
-    P->nparts = std::max(P->tf.grid, P->ta.grid);
+    P->nparts = std::max(std::max(P->tf.grid, P->ta.grid), fft_epilogue_blocks());
     P->gp = GradPsfPlan{P->m[0], P->m[1], P->m[2], P->q[0], P->q[1], P->q[2], 1,
                         std::max(1, (152 * 4 + P->q[0] - 1) / P->q[0])};
 
@@ -382,6 +392,7 @@ cdv_status cdv_plan_create(cdv_plan** out, int n, const int64_t* m, const int32_
             return fail(CDV_ERR_UNSUPPORTED, "no tensor-core kernel for this size (template rows > 129 or too wide)");
         }
     }
+    if (e == cudaSuccess && P->fft()) e = fft_setup(P->fftp, P->gf, plan_alloc, P);
     if (e == cudaSuccess) e = P->alloc(&P->H, P->nh);
     if (e == cudaSuccess) e = P->alloc(&P->Ht, P->nh);
     if (e == cudaSuccess) e = P->alloc(&P->absum, 1);
@@ -435,6 +446,8 @@ cdv_status cdv_plan_set_psf(cdv_plan* plan, const float* H, void* stream)
                                  (int)plan->mode, const_cast<void*>(plan->tca.bt[0]),
                                  const_cast<void*>(plan->tca.bt[1]), s), "Toeplitz tiles (adjoint)");
     }
+    if (plan->fft())
+        CDV_CUDA(fft_set_psf(plan->fftp, plan->H, plan->q[0], plan->q[1], plan->q[2], s), "template spectrum");
     plan->has_psf = true;
     return CDV_OK;
 }
@@ -483,7 +496,9 @@ cdv_status cdv_plan_describe(const cdv_plan* plan, cdv_plan_info* out)
     out->mode = (int32_t)plan->mode;
     out->algorithmic_macs = (double)plan->nx * (double)plan->nh;
     for (int d = 0; d < 2; d++) {
-        if (plan->mode == CDV_MODE_FP32) {
+        if (plan->fft()) {
+            continue;
+        } else if (plan->mode == CDV_MODE_FP32) {
             const ConvTile& c = d ? plan->ta : plan->tf;
             out->grid[d] = c.grid;
             out->tiles[d] = c.grid;
@@ -513,6 +528,14 @@ static cdv_status run_conv(cdv_plan* P, bool fwd, int batch, const float* in, fl
     if (!in || !out) return fail(CDV_ERR_INVALID_ARG, "NULL array");
     if (batch < 1 || batch > 65535) return fail(CDV_ERR_INVALID_ARG, "batch = %d", batch);
     if (!P->has_psf) return fail(CDV_ERR_NO_PSF, "no template set");
+    if (P->fft()) {
+        const ConvGeom& g = fwd ? P->gf : P->ga;
+        for (int b = 0; b < batch; b++)
+            CDV_CUDA(fft_conv(P->fftp, g, fwd, in + (int64_t)b * (fwd ? P->nx : P->ny),
+                              out + (int64_t)b * (fwd ? P->ny : P->nx), s),
+                     fwd ? "forward (FFT)" : "adjoint (FFT)");
+        return CDV_OK;
+    }
     if (P->tc()) {
         const ConvGeom& g = fwd ? P->gf : P->ga;
         for (int b = 0; b < batch; b++) {
@@ -603,7 +626,9 @@ static cdv_status run_phase(void* vctx, int phase, bool loop, unsigned long long
     const IterCtx c = make_ctx(P, R.Y, R.X);
     const int max_trials = R.K + R.o.max_rejects + 1;
     int nf, nm;
-    if (P->tc()) {
+    if (P->fft()) {
+        nf = nm = fft_epilogue_blocks();
+    } else if (P->tc()) {
         nf = P->tcf.grid;
         nm = P->tca.grid;
     } else {
@@ -622,7 +647,9 @@ static cdv_status run_phase(void* vctx, int phase, bool loop, unsigned long long
         CDV_CUDA(launch_state_init(P->st, R.o.delta0, P->absum, R.o.beta, R.o.max_halvings, R.o.max_rejects, R.K,
                                    kHistCap, R.o.tikhonov, R.o.armijo, R.o.bb, s), "state");
         if (R.o.tikhonov != 0.0) CDV_CUDA(launch_sumsq(R.X, P->nx, P->part_x, s), "||x_0||^2");
-        if (P->tc()) {
+        if (P->fft()) {
+            CDV_CUDA(fft_role(P->fftp, P->gf, ROLE_FWD_INIT, c, s), "forward (initial, FFT)");
+        } else if (P->tc()) {
             TcArgs F = P->tcf;
             F.ctx = c;
             F.role = ROLE_FWD_INIT;
@@ -638,7 +665,10 @@ static cdv_status run_phase(void* vctx, int phase, bool loop, unsigned long long
         }
         CDV_CUDA(decide(1), "decide (initial)");
     } else if (phase == 1) {
-        if (P->tc()) {
+        if (P->fft()) {
+            CDV_CUDA(fft_role(P->fftp, P->ga, ROLE_ADJ_TRIAL, c, s), "adjoint trial (FFT)");
+            CDV_CUDA(fft_role(P->fftp, P->gf, ROLE_FWD_TRIAL, c, s), "forward trial (FFT)");
+        } else if (P->tc()) {
             TcArgs F = P->tcf, A = P->tca;
             F.ctx = c;
             A.ctx = c;
@@ -722,7 +752,7 @@ cdv_status cdv_iterate(cdv_plan* plan, const float* Y, float* X, int K, const cd
     const bool plain_rule = o.tikhonov == 0.0 && o.armijo == 0.0 && o.bb == 0;
     const double delta0 = o.delta0 > 0.0 ? o.delta0 : 0.0;
     cudaStream_t s = (cudaStream_t)stream;
-    const bool small_ok = !plan->tc() && small_supported(plan->m, plan->p);
+    const bool small_ok = plan->mode == CDV_MODE_FP32 && small_supported(plan->m, plan->p);
     if (o.path == CDV_PATH_SMALL && !small_ok)
         return fail(CDV_ERR_UNSUPPORTED, "problem does not fit the single-CTA path (%zu bytes of shared memory)",
                     small_smem_bytes(plan->m, plan->p));
@@ -804,7 +834,7 @@ cdv_status cdv_iterate_host(cdv_plan* plan, const float* Y_host, float* X_host, 
 cdv_status cdv_richardson_lucy(cdv_plan* plan, const float* Y, float* X, int K, void* stream)
 {
     if (!plan || !Y || !X) return fail(CDV_ERR_INVALID_ARG, "NULL argument");
-    if (plan->tc()) return fail(CDV_ERR_UNSUPPORTED, "Richardson-Lucy runs in CDV_MODE_FP32 only");
+    if (plan->mode != CDV_MODE_FP32) return fail(CDV_ERR_UNSUPPORTED, "Richardson-Lucy runs in CDV_MODE_FP32 only");
     if (K < 0) return fail(CDV_ERR_INVALID_ARG, "K = %d", K);
     if (!plan->has_psf) return fail(CDV_ERR_NO_PSF, "no template set");
     cudaStream_t s = (cudaStream_t)stream;

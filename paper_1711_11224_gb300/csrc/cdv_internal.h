@@ -211,6 +211,23 @@ cudaError_t tc_build_btiles(const float* w, int q1, int q2, int q3, int D, int K
 cudaError_t tc_shadow(const float* src, int64_t a1a2, int64_t a3, int64_t pitch, int kind, void* hi, void* lo,
                       cudaStream_t s);
 
+// FFT comparator (fft.cu): cuFFT plans over the zero-padded grid of N_i >= m_i + 2p_i samples.
+struct FftPlan {
+    int64_t N[3] = {1, 1, 1};
+    int64_t nreal = 0, ncplx = 0;
+    int r2c = 0, c2r = 0;     // cufftHandle
+    bool have_plans = false;
+    float* real = nullptr;    // nreal floats
+    void* spec = nullptr;     // ncplx cufftComplex: the transform of the current input
+    void* hspec = nullptr;    // ncplx cufftComplex: transform of the zero-padded template / prod(N)
+};
+int fft_epilogue_blocks();
+cudaError_t fft_setup(FftPlan& F, const ConvGeom& gf, void* (*alloc)(void* owner, size_t bytes), void* owner);
+void fft_release(FftPlan& F);
+cudaError_t fft_set_psf(FftPlan& F, const float* H, int q1, int q2, int q3, cudaStream_t s);
+cudaError_t fft_conv(FftPlan& F, const ConvGeom& g, bool fwd, const float* in, float* out, cudaStream_t s);
+cudaError_t fft_role(FftPlan& F, const ConvGeom& g, int role, const IterCtx& c, cudaStream_t s);
+
 // Message returned by cdv_last_error() on this host thread (capi.cu).
 void set_last_error(const char* msg);
 
