@@ -89,6 +89,11 @@ struct cdv_batch {
     int2* d_items_f = nullptr;
     int2* d_items_a = nullptr;
     cudaStream_t cap = nullptr;
+    // one stream per template-width group: the groups' launches of a trial slot run side by side
+    // (captured as parallel graph branches), joined before the decision
+    std::vector<cudaStream_t> gstream;
+    std::vector<cudaEvent_t> gdone;
+    cudaEvent_t fork = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     std::vector<const float*> key_y;
@@ -118,6 +123,12 @@ struct cdv_batch {
         allocs.clear();
         if (cap) cudaStreamDestroy(cap);
         cap = nullptr;
+        for (cudaStream_t t : gstream) cudaStreamDestroy(t);
+        gstream.clear();
+        for (cudaEvent_t t : gdone) cudaEventDestroy(t);
+        gdone.clear();
+        if (fork) cudaEventDestroy(fork);
+        fork = nullptr;
     }
 };
 
@@ -272,6 +283,15 @@ cdv_status cdv_batch_plan_create(cdv_batch** out, int count, int n, const int64_
         gr.n_a = (int)items_a.size() - gr.off_a;
         if (gr.n_f > 0) B->groups.push_back(gr);
     }
+    for (size_t i = 0; e == cudaSuccess && i < B->groups.size(); i++) {
+        cudaStream_t t = nullptr;
+        cudaEvent_t d = nullptr;
+        e = cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking);
+        if (e == cudaSuccess) B->gstream.push_back(t);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d, cudaEventDisableTiming);
+        if (e == cudaSuccess) B->gdone.push_back(d);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = B->alloc(&B->d_items_f, items_f.size());
     if (e == cudaSuccess) e = B->alloc(&B->d_items_a, items_a.size());
     if (e == cudaSuccess)
@@ -360,6 +380,28 @@ struct BatchRun {
     cdv_iter_opts o;
 };
 
+// The convolutions of one slot: per template-width group (its own stream, forked from s) the adjoint
+// trial then the forward trial (trial), or the initial forward (prologue); all groups joined back
+// into s.  A volume belongs to one group, so its adjoint precedes its forward; groups are independent.
+static cdv_status batch_groups(cdv_batch* b, bool trial, cudaStream_t s)
+{
+    BCUDA(cudaEventRecord(b->fork, s), "fork");
+    for (size_t i = 0; i < b->groups.size(); i++) {
+        const auto& g = b->groups[i];
+        cudaStream_t t = b->gstream[i];
+        BCUDA(cudaStreamWaitEvent(t, b->fork, 0), "fork wait");
+        if (trial) {
+            BCUDA(conv_fp32_batch_launch(g.q3, b->d_adj_trial, b->d_items_a + g.off_a, g.n_a, g.smem_a, t), "adjoint");
+            BCUDA(conv_fp32_batch_launch(g.q3, b->d_fwd_trial, b->d_items_f + g.off_f, g.n_f, g.smem_f, t), "forward");
+        } else {
+            BCUDA(conv_fp32_batch_launch(g.q3, b->d_fwd_init, b->d_items_f + g.off_f, g.n_f, g.smem_f, t), "forward");
+        }
+        BCUDA(cudaEventRecord(b->gdone[i], t), "join");
+        BCUDA(cudaStreamWaitEvent(s, b->gdone[i], 0), "join wait");
+    }
+    return CDV_OK;
+}
+
 // Phases of a batched run (see build_loop_graph): 0 prologue, 1 one trial slot for every volume,
 // 2 epilogue.  In a loop graph the slot ends with the loop condition (any volume still running).
 static cdv_status batch_phase(void* vctx, int phase, bool loop, unsigned long long h, cudaStream_t s)
@@ -371,14 +413,12 @@ static cdv_status batch_phase(void* vctx, int phase, bool loop, unsigned long lo
         BCUDA(launch_batch_x0(b->d_ctx, b->count, R.o.x0_policy, s), "x0");
         BCUDA(launch_batch_state_init(b->d_ctx, b->count, R.o.delta0 > 0.0 ? R.o.delta0 : 0.0, R.o.beta,
                                       R.o.max_halvings, R.o.max_rejects, R.K, kBatchHist, s), "state");
-        for (const auto& g : b->groups)
-            BCUDA(conv_fp32_batch_launch(g.q3, b->d_fwd_init, b->d_items_f + g.off_f, g.n_f, g.smem_f, s), "forward");
+        cdv_status st = batch_groups(b, false, s);
+        if (st != CDV_OK) return st;
         BCUDA(launch_batch_decide(b->d_ctx, b->count, 1, s), "decide");
     } else if (phase == 1) {
-        for (const auto& g : b->groups)
-            BCUDA(conv_fp32_batch_launch(g.q3, b->d_adj_trial, b->d_items_a + g.off_a, g.n_a, g.smem_a, s), "adjoint");
-        for (const auto& g : b->groups)
-            BCUDA(conv_fp32_batch_launch(g.q3, b->d_fwd_trial, b->d_items_f + g.off_f, g.n_f, g.smem_f, s), "forward");
+        cdv_status st = batch_groups(b, true, s);
+        if (st != CDV_OK) return st;
         BCUDA(launch_batch_decide(b->d_ctx, b->count, 0, s), "decide");
     } else {
         BCUDA(launch_batch_finalize(b->d_ctx, b->count, s), "finalize");
