@@ -333,7 +333,7 @@ def run_batch(args):
     ev1 = torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
         ev0.record(stream)
-        _, reps = bp.iterate(Ys, Xs, K=K, x0="crop")
+        _, reps = bp.iterate(Ys, Xs, K=K, x0="crop", use_graph=not args.no_graph)
         ev1.record(stream)
         torch.cuda.synchronize()
     t = ev0.elapsed_time(ev1) / 1e3
