@@ -35,6 +35,7 @@
 namespace cdv {
 
 constexpr int kR3 = 8;        // outputs per thread along the contiguous axis
+static_assert(kR3 == 8, "the input-tile chunk order assumes windows that start every two chunks");
 constexpr int kT1 = 4;        // output planes per CTA (and per thread)
 constexpr int kMaxThreads = 256;
 
@@ -66,18 +67,26 @@ __device__ __forceinline__ double block_sum_f64(double v, double* s_red)
 
 // Shared-memory layout of one CTA (in floats):
 //   [input tile, 2 buffers][template ring, T1+1 planes][running totals][FP64 scratch]
+// Each input-tile row stores its 16-byte chunks even chunks first, then odd
+// chunks (chunk c at slot c/2, or neven + c/2 for odd c).  A thread's window
+// of R3 = 8 columns starts at chunk 2*tx, so its k-th float4 load is chunk
+// 2*tx + k: in this order consecutive threads read consecutive slots and the
+// 128-bit loads are free of bank conflicts (in column order the 32-byte
+// stride between threads puts two threads of each quarter warp on the same
+// banks).
 // The template ring holds plane j1 in slot j1 mod (T1+1): consecutive input
 // planes u need the template planes j1 = s1 + o1 - u of the CTA's T1 output
 // planes, a window that slides by one plane per u, so one new plane is staged
 // per input plane.  Running totals are stored [T1*R3][threads] (thread index
 // fastest: conflict-free).
 struct ConvSmem {
-    int rows, pitch, tile_in, wplane, tile_w, tot;
+    int rows, pitch, neven, tile_in, wplane, tile_w, tot;
     __host__ __device__ static ConvSmem make(int ntx, int nty, int q2, int q3)
     {
         ConvSmem s;
         s.rows = nty + q2 - 1;
         s.pitch = ceil4((ntx - 1) * kR3 + ceil4(kR3 + q3 - 1));
+        s.neven = (s.pitch / 4 + 1) / 2;
         s.tile_in = s.rows * s.pitch;
         s.wplane = q2 * ceil4(q3);
         s.tile_w = (kT1 + 1) * s.wplane;
@@ -179,7 +188,9 @@ __device__ __forceinline__ void conv_fp32_body(const ConvLaunch& L, const int nt
                 for (int c = lane; c < lay.pitch; c += 32) {
                     const int64_t t = c0 + c;
                     const bool ok = rok && (t >= 0) && (t < G.a3);
-                    cp_async4(dst + r * lay.pitch + c, ok ? src + t : in, ok);
+                    const int c4 = c >> 2;
+                    const int slot = (c4 & 1) ? lay.neven + (c4 >> 1) : (c4 >> 1);
+                    cp_async4(dst + r * lay.pitch + slot * 4 + (c & 3), ok ? src + t : in, ok);
                 }
             }
         };
@@ -220,13 +231,15 @@ __device__ __forceinline__ void conv_fp32_body(const ConvLaunch& L, const int nt
 #pragma unroll
                     for (int c = 0; c < R3; c++) part[i][c] = 0.f;
 
-                const float* sin = s_in0 + buf * lay.tile_in + tx * R3;
+                const float* sin = s_in0 + buf * lay.tile_in + tx * 4;      // chunk 2*tx: even slot tx
+                const int odd = lay.neven * 4;
                 for (int j2 = j2lo; j2 <= j2hi; ++j2) {
                     const float* src = sin + (ty + q2 - 1 - j2) * lay.pitch;
                     float wv[WLP];
 #pragma unroll
                     for (int i = 0; i < WLP; i += 4) {
-                        const float4 v = *reinterpret_cast<const float4*>(src + i);
+                        const int k = i >> 2;                   // chunk 2*tx + k
+                        const float4 v = *reinterpret_cast<const float4*>(src + ((k & 1) ? odd : 0) + (k >> 1) * 4);
                         wv[i] = v.x; wv[i + 1] = v.y; wv[i + 2] = v.z; wv[i + 3] = v.w;
                     }
 #pragma unroll
