@@ -60,9 +60,12 @@ typedef enum {
     CDV_MODE_BF16 = 1,          /* tensor cores, BF16 products, FP32 accumulate */
     CDV_MODE_TF32 = 2,          /* tensor cores, TF32 products, FP32 accumulate */
     CDV_MODE_SPLIT_BF16X3 = 3,  /* tensor cores, x_hi h_hi + x_hi h_lo + x_lo h_hi */
-    CDV_MODE_FFT = 4            /* comparator, not the paper's method: both operators through FP32
+    CDV_MODE_FFT = 4,           /* comparator, not the paper's method: both operators through FP32
                                    cuFFT transforms of a zero-padded grid (the FFT approach the
                                    paper's introduction contrasts with); same iteration and reports */
+    CDV_MODE_SEPARABLE = 5      /* template given as per-axis factors (cdv_plan_set_psf_factors):
+                                   both operators as one 1-D FP32 pass per axis; same iteration,
+                                   decisions and reports as the direct modes */
 } cdv_mode;
 
 typedef struct cdv_plan cdv_plan;
@@ -98,6 +101,23 @@ cdv_status cdv_plan_workspace_size(const cdv_plan* plan, size_t* bytes);
  */
 cdv_status cdv_plan_set_psf(cdv_plan* plan, const float* H, void* stream);
 
+/*
+ * Set a separable template H(j_1, .., j_n) = h_1(j_1) ... h_n(j_n) on a
+ * CDV_MODE_SEPARABLE plan.  `h` is a host array of n device pointers; h[i]
+ * holds the 2p_i + 1 float32 samples of the factor along axis i (axis n is
+ * the contiguous one).  The plan copies the factors, builds the dense H from
+ * them (for sum_j |h(j)| and the default step length, as cdv_plan_set_psf
+ * does) and from then on computes both operators axis by axis: with a
+ * product template the block-Toeplitz matrix of Property 1 is the Kronecker
+ * product of the per-axis Toeplitz matrices, so the forward operator is a 1-D
+ * full convolution along each axis (m_i -> m_i + 2p_i) and the adjoint of
+ * Property 2 a 1-D valid correlation along each axis (m_i + 2p_i -> m_i).
+ * Factors of 1..31 samples per axis.  CDV_ERR_UNSUPPORTED on a plan of any
+ * other mode (and cdv_plan_set_psf returns it on a separable plan).
+ * Asynchronous on `stream`, like cdv_plan_set_psf.
+ */
+cdv_status cdv_plan_set_psf_factors(cdv_plan* plan, const float* const* h, void* stream);
+
 /* Lipschitz bound L = (sum |h|)^2 of the current template (host value).
  * Synchronises the device. */
 cdv_status cdv_plan_lipschitz(const cdv_plan* plan, double* L);
@@ -111,7 +131,9 @@ cdv_status cdv_plan_lipschitz(const cdv_plan* plan, double* L);
  * along the contiguous axis and `executed_macs` the multiply-adds the tensor
  * pipe performs per launch, all products of split-BF16x3 included (padding
  * of K, of ragged tiles and of odd plane counts counted too).  For the FP32
- * engine cols = K = 0 and executed_macs = algorithmic_macs; for CDV_MODE_FFT all are 0.  `grid` is the
+ * engine cols = K = 0 and executed_macs = algorithmic_macs; for CDV_MODE_FFT all are 0; for
+ * CDV_MODE_SEPARABLE executed_macs counts the three 1-D passes (outputs x taps of each) and
+ * algorithmic_macs stays the dense count prod(m) prod(2p+1).  `grid` is the
  * number of CTAs of one launch.  Host-only: no device work.
  */
 typedef struct cdv_plan_info {

@@ -19,7 +19,7 @@ STATUS = {
     5: "CDV_ERR_CUDA", 6: "CDV_ERR_TIMEOUT", 7: "CDV_ERR_NOT_DESCENDING", 8: "CDV_ERR_NONFINITE",
     9: "CDV_ERR_NO_PSF",
 }
-MODES = {"fp32": 0, "bf16": 1, "tf32": 2, "split3": 3, "fft": 4}
+MODES = {"fp32": 0, "bf16": 1, "tf32": 2, "split3": 3, "fft": 4, "separable": 5}
 X0 = {"given": 0, "crop": 1, "zero": 2}
 PATHS = {"auto": 0, "general": 1, "small": 2}
 
@@ -29,7 +29,7 @@ EXPORTS = [
     "cdv_plan_set_psf", "cdv_plan_lipschitz", "cdv_plan_destroy", "cdv_forward", "cdv_adjoint", "cdv_grad_psf",
     "cdv_iter_opts_default", "cdv_iterate", "cdv_iterate_host", "cdv_richardson_lucy", "cdv_plan_sync_status",
     "cdv_grad_psf_static", "cdv_batch_plan_create", "cdv_batch_workspace_size", "cdv_batch_set_psfs",
-    "cdv_batch_iterate", "cdv_batch_destroy", "cdv_plan_describe",
+    "cdv_batch_iterate", "cdv_batch_destroy", "cdv_plan_describe", "cdv_plan_set_psf_factors",
 ]
 
 
@@ -82,6 +82,7 @@ def load(path=LIB_PATH):
     lib.cdv_plan_create.argtypes = [ctypes.POINTER(vp), i32, i64p, ctypes.POINTER(ctypes.c_int32), i32, vp]
     lib.cdv_plan_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
     lib.cdv_plan_set_psf.argtypes = [vp, vp, vp]
+    lib.cdv_plan_set_psf_factors.argtypes = [vp, ctypes.POINTER(vp), vp]
     lib.cdv_plan_lipschitz.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     lib.cdv_plan_destroy.argtypes = [vp]
     lib.cdv_plan_describe.argtypes = [vp, ctypes.POINTER(PlanInfo)]

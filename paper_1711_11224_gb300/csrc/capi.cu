@@ -89,6 +89,8 @@ struct cdv_plan {
     bool tc() const { return mode == CDV_MODE_BF16 || mode == CDV_MODE_TF32 || mode == CDV_MODE_SPLIT_BF16X3; }
     bool fft() const { return mode == CDV_MODE_FFT; }
     FftPlan fftp{};
+    bool sep() const { return mode == CDV_MODE_SEPARABLE; }
+    SepPlan sepp{};
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -326,7 +328,7 @@ cdv_status cdv_plan_create(cdv_plan** out, int n, const int64_t* m, const int32_
     if (!m || !p) return fail(CDV_ERR_INVALID_ARG, "m or p is NULL");
     if (n < 1 || n > 3) return fail(CDV_ERR_SHAPE, "n = %d, must be 1, 2 or 3", n);
     if (mode != CDV_MODE_FP32 && mode != CDV_MODE_BF16 && mode != CDV_MODE_TF32 && mode != CDV_MODE_SPLIT_BF16X3 &&
-        mode != CDV_MODE_FFT)
+        mode != CDV_MODE_FFT && mode != CDV_MODE_SEPARABLE)
         return fail(CDV_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
     for (int i = 0; i < n; i++) {
         if (m[i] < 1) return fail(CDV_ERR_SHAPE, "m[%d] = %lld < 1", i, (long long)m[i]);
@@ -358,6 +360,10 @@ cdv_status cdv_plan_create(cdv_plan** out, int n, const int64_t* m, const int32_
         return fail(CDV_ERR_UNSUPPORTED, "template width %d along the contiguous axis: this build supports odd 1..31",
                     P->q[2]);
     }
+    if (mode == CDV_MODE_SEPARABLE && !sep_supported(P->q)) {
+        delete P;
+        return fail(CDV_ERR_UNSUPPORTED, "separable template: this build supports odd 1..31 samples per axis");
+    }
     P->gf = ConvGeom{P->m[0], P->m[1], P->m[2],
                      P->m[0] + 2 * P->p[0], P->m[1] + 2 * P->p[1], P->m[2] + 2 * P->p[2],
                      0, 0, 0, P->q[0], P->q[1], P->q[2]};
@@ -365,7 +371,7 @@ cdv_status cdv_plan_create(cdv_plan** out, int n, const int64_t* m, const int32_
                      2 * P->p[0], 2 * P->p[1], 2 * P->p[2], P->q[0], P->q[1], P->q[2]};
     P->tf = conv_fp32_tile(P->gf);
     P->ta = conv_fp32_tile(P->ga);
-    P->nparts = std::max(std::max(P->tf.grid, P->ta.grid), fft_epilogue_blocks());
+    P->nparts = std::max(std::max(P->tf.grid, P->ta.grid), std::max(fft_epilogue_blocks(), sep_blocks()));
     P->gp = GradPsfPlan{P->m[0], P->m[1], P->m[2], P->q[0], P->q[1], P->q[2], 1,
                         std::max(1, (152 * 4 + P->q[0] - 1) / P->q[0])};
 
@@ -393,6 +399,7 @@ cdv_status cdv_plan_create(cdv_plan** out, int n, const int64_t* m, const int32_
         }
     }
     if (e == cudaSuccess && P->fft()) e = fft_setup(P->fftp, P->gf, plan_alloc, P);
+    if (e == cudaSuccess && P->sep()) e = sep_setup(P->sepp, P->m, P->p, plan_alloc, P);
     if (e == cudaSuccess) e = P->alloc(&P->H, P->nh);
     if (e == cudaSuccess) e = P->alloc(&P->Ht, P->nh);
     if (e == cudaSuccess) e = P->alloc(&P->absum, 1);
@@ -433,6 +440,9 @@ cdv_status cdv_plan_workspace_size(const cdv_plan* plan, size_t* bytes)
 cdv_status cdv_plan_set_psf(cdv_plan* plan, const float* H, void* stream)
 {
     if (!plan || !H) return fail(CDV_ERR_INVALID_ARG, "NULL argument");
+    if (plan->sep())
+        return fail(CDV_ERR_UNSUPPORTED, "a separable plan takes its template as per-axis factors "
+                                         "(cdv_plan_set_psf_factors)");
     cudaStream_t s = (cudaStream_t)stream;
     CDV_CUDA(cudaMemcpyAsync(plan->H, H, plan->nh * sizeof(float), cudaMemcpyDeviceToDevice, s), "copy H");
     CDV_CUDA(launch_flip(plan->H, plan->Ht, plan->q[0], plan->q[1], plan->q[2], s), "flip H");
@@ -448,6 +458,23 @@ cdv_status cdv_plan_set_psf(cdv_plan* plan, const float* H, void* stream)
     }
     if (plan->fft())
         CDV_CUDA(fft_set_psf(plan->fftp, plan->H, plan->q[0], plan->q[1], plan->q[2], s), "template spectrum");
+    plan->has_psf = true;
+    return CDV_OK;
+}
+
+cdv_status cdv_plan_set_psf_factors(cdv_plan* plan, const float* const* h, void* stream)
+{
+    if (!plan || !h) return fail(CDV_ERR_INVALID_ARG, "NULL argument");
+    if (!plan->sep()) return fail(CDV_ERR_UNSUPPORTED, "per-axis factors need a CDV_MODE_SEPARABLE plan");
+    const float* hp[3] = {nullptr, nullptr, nullptr};
+    for (int i = 0; i < plan->n; i++) {
+        if (!h[i]) return fail(CDV_ERR_INVALID_ARG, "factor %d is NULL", i);
+        hp[3 - plan->n + i] = h[i];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    CDV_CUDA(sep_set_factors(plan->sepp, hp, plan->q, plan->H, s), "separable factors");
+    CDV_CUDA(launch_flip(plan->H, plan->Ht, plan->q[0], plan->q[1], plan->q[2], s), "flip H");
+    CDV_CUDA(launch_abs_sum(plan->H, plan->nh, plan->absum, s), "sum |H|");
     plan->has_psf = true;
     return CDV_OK;
 }
@@ -498,6 +525,9 @@ cdv_status cdv_plan_describe(const cdv_plan* plan, cdv_plan_info* out)
     for (int d = 0; d < 2; d++) {
         if (plan->fft()) {
             continue;
+        } else if (plan->sep()) {
+            out->grid[d] = sep_blocks();
+            out->executed_macs[d] = sep_pass_macs(plan->sepp, d == 0);
         } else if (plan->mode == CDV_MODE_FP32) {
             const ConvTile& c = d ? plan->ta : plan->tf;
             out->grid[d] = c.grid;
@@ -528,6 +558,13 @@ static cdv_status run_conv(cdv_plan* P, bool fwd, int batch, const float* in, fl
     if (!in || !out) return fail(CDV_ERR_INVALID_ARG, "NULL array");
     if (batch < 1 || batch > 65535) return fail(CDV_ERR_INVALID_ARG, "batch = %d", batch);
     if (!P->has_psf) return fail(CDV_ERR_NO_PSF, "no template set");
+    if (P->sep()) {
+        for (int b = 0; b < batch; b++)
+            CDV_CUDA(sep_conv(P->sepp, fwd, in + (int64_t)b * (fwd ? P->nx : P->ny),
+                              out + (int64_t)b * (fwd ? P->ny : P->nx), s),
+                     fwd ? "forward (separable)" : "adjoint (separable)");
+        return CDV_OK;
+    }
     if (P->fft()) {
         const ConvGeom& g = fwd ? P->gf : P->ga;
         for (int b = 0; b < batch; b++)
@@ -628,6 +665,8 @@ static cdv_status run_phase(void* vctx, int phase, bool loop, unsigned long long
     int nf, nm;
     if (P->fft()) {
         nf = nm = fft_epilogue_blocks();
+    } else if (P->sep()) {
+        nf = nm = sep_blocks();
     } else if (P->tc()) {
         nf = P->tcf.grid;
         nm = P->tca.grid;
@@ -649,6 +688,8 @@ static cdv_status run_phase(void* vctx, int phase, bool loop, unsigned long long
         if (R.o.tikhonov != 0.0) CDV_CUDA(launch_sumsq(R.X, P->nx, P->part_x, s), "||x_0||^2");
         if (P->fft()) {
             CDV_CUDA(fft_role(P->fftp, P->gf, ROLE_FWD_INIT, c, s), "forward (initial, FFT)");
+        } else if (P->sep()) {
+            CDV_CUDA(sep_role(P->sepp, true, ROLE_FWD_INIT, c, s), "forward (initial, separable)");
         } else if (P->tc()) {
             TcArgs F = P->tcf;
             F.ctx = c;
@@ -668,6 +709,9 @@ static cdv_status run_phase(void* vctx, int phase, bool loop, unsigned long long
         if (P->fft()) {
             CDV_CUDA(fft_role(P->fftp, P->ga, ROLE_ADJ_TRIAL, c, s), "adjoint trial (FFT)");
             CDV_CUDA(fft_role(P->fftp, P->gf, ROLE_FWD_TRIAL, c, s), "forward trial (FFT)");
+        } else if (P->sep()) {
+            CDV_CUDA(sep_role(P->sepp, false, ROLE_ADJ_TRIAL, c, s), "adjoint trial (separable)");
+            CDV_CUDA(sep_role(P->sepp, true, ROLE_FWD_TRIAL, c, s), "forward trial (separable)");
         } else if (P->tc()) {
             TcArgs F = P->tcf, A = P->tca;
             F.ctx = c;

@@ -228,6 +228,49 @@ cudaError_t fft_set_psf(FftPlan& F, const float* H, int q1, int q2, int q3, cuda
 cudaError_t fft_conv(FftPlan& F, const ConvGeom& g, bool fwd, const float* in, float* out, cudaStream_t s);
 cudaError_t fft_role(FftPlan& F, const ConvGeom& g, int role, const IterCtx& c, cudaStream_t s);
 
+// Unsigned 32-bit division by a divisor fixed at plan time, as a multiply-high and two shifts
+// (Granlund and Montgomery, "Division by invariant integers using multiplication", 1994).
+struct FastDiv {
+    uint32_t m;
+    int s1, s2;
+};
+FastDiv make_fastdiv(uint32_t d);
+
+// Separable-template engine (sep.cu).  One 1-D pass over a volume viewed as (outer, kin, inner):
+//   out[u, s, i] = sum_{j < q} w[j] in[u, s + o - j, i]   (in = 0 outside [0, kin))
+struct SepPass {
+    const float* in;     // null on the first pass of a role launch: chosen from the iteration state
+    float* out;          // null on the last pass of a role launch: the epilogue's buffers
+    const float* w;      // q taps
+    int64_t outer, kin, kout, inner;
+    int q, o;
+    int first, last;
+    int role;
+    int seg, rb;         // rows kernel (inner == 1): outputs per segment (multiple of 7), rows per task
+    FastDiv dspan, dcpr, dseg;   // rows kernel: division by seg + q - 1, seg / 7 and seg
+    int64_t strip;       // cols kernel: outputs per warp task (multiple of 8)
+    IterCtx c;
+};
+struct SepPlan {
+    float* hf = nullptr;     // factors h_1 | h_2 | h_3 (q1 + q2 + q3 floats)
+    float* hb = nullptr;     // the same, each reversed (the factors of H~)
+    float* tA = nullptr;     // intermediates, m1 x (m2 + 2p2) x (m3 + 2p3) floats each
+    float* tB = nullptr;
+    SepPass fwd[3], adj[3];
+};
+int sep_blocks();
+bool sep_supported(const int q[3]);
+cudaError_t sep_setup(SepPlan& S, const int64_t m[3], const int p[3], void* (*alloc)(void* owner, size_t bytes),
+                      void* owner);
+// h[a]: device pointer to q[a] floats (null: the axis has q[a] == 1 and factor 1); H receives the
+// dense outer product.
+cudaError_t sep_set_factors(SepPlan& S, const float* const h[3], const int q[3], float* H, cudaStream_t s);
+cudaError_t sep_conv(const SepPlan& S, bool fwd, const float* in, float* out, cudaStream_t s);
+cudaError_t sep_role(const SepPlan& S, bool fwd, int role, const IterCtx& c, cudaStream_t s);
+double sep_pass_macs(const SepPlan& S, bool fwd);
+template <int Q, bool EPI>
+cudaError_t sep_launch_q(const SepPass& P, int blocks, cudaStream_t s);
+
 // Message returned by cdv_last_error() on this host thread (capi.cu).
 void set_last_error(const char* msg);
 

@@ -89,6 +89,18 @@ class Plan:
         self.H = H
         return self
 
+    def set_psf_factors(self, hs):
+        """Separable template H = h_1 x .. x h_n (mode "separable"): one device tensor of 2p_i+1 samples per axis."""
+        hs = list(hs)
+        if len(hs) != self.n:
+            raise ValueError("expected %d factors, got %d" % (self.n, len(hs)))
+        for i, h in enumerate(hs):
+            _need(h, (self.q[i],), "h[%d]" % i)
+        arr = (ctypes.c_void_p * self.n)(*[h.data_ptr() for h in hs])
+        B.check(self.lib.cdv_plan_set_psf_factors(self._h, arr, _stream()))
+        self.H = hs
+        return self
+
     def lipschitz(self):
         v = ctypes.c_double()
         B.check(self.lib.cdv_plan_lipschitz(self._h, ctypes.byref(v)))

@@ -32,7 +32,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = [
-    "Problem", "gaussian_psf", "ring_psf", "blobs", "filaments", "observe",
+    "Problem", "gaussian_psf", "gaussian_factors", "ring_psf", "blobs", "filaments", "observe",
     "blobs2d", "fil3d", "grad3d", "ring3d", "batch64", "batch64_shapes",
     "scaled_fil3d", "integer_case", "random_case", "WORKLOADS",
 ]
@@ -71,6 +71,16 @@ def gaussian_psf(q, sigma):
         e += g * g / (2.0 * s * s)
     h = np.exp(-e)
     return (h / h.sum()).astype(np.float32)
+
+
+def gaussian_factors(q, sigma):
+    """Per-axis factors of gaussian_psf(q, sigma): 1-D Gaussians, each sum 1 (their outer product is the template)."""
+    out = []
+    for n, s in zip(q, sigma):
+        g = np.arange(int(n), dtype=np.float64) - (int(n) - 1) / 2
+        h = np.exp(-g * g / (2.0 * float(s) * float(s)))
+        out.append((h / h.sum()).astype(np.float32))
+    return out
 
 
 def ring_psf(q=(31, 31, 21), sigma=(2.0, 2.0, 4.0), ring_r=10.0, ring_w=1.5, ring_amp=0.2, ring_sz=4.0):
