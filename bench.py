@@ -82,9 +82,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cdv", choices=["cdv", "reference"])
     ap.add_argument("--workload", default="ring3d", choices=sorted(WORKLOADS))
-    ap.add_argument("--mode", default="split3", choices=["fp32", "bf16", "tf32", "split3", "fft"],
+    ap.add_argument("--mode", default="split3", choices=["fp32", "bf16", "tf32", "split3", "fft", "separable"],
                     help="arithmetic of the convolutions (default: split-BF16x3, the fastest form within the FP32 "
-                         "accuracy bar; fft: the cuFFT comparator, not the paper's method)")
+                         "accuracy bar; fft: the cuFFT comparator, not the paper's method; separable: the "
+                         "template as 1-D factors, --kernels-only on the Gaussian workloads)")
     ap.add_argument("--no-forms", action="store_true", help="skip the per-form kernel timings and errors")
     ap.add_argument("--path", default="auto", choices=["auto", "general", "small"])
     ap.add_argument("--no-e2e", action="store_true")
@@ -101,6 +102,24 @@ def parse():
 def problem(name):
     import synth
     return {"ring3d": synth.ring3d, "fil3d": synth.fil3d, "blobs2d": synth.blobs2d, "batch64": synth.batch64}[name]()
+
+
+# Gaussian templates of the workloads, as (samples, sigma) per axis: their 1-D factors for the separable mode
+SEPARABLE = {"fil3d": ((15, 15, 11), (1.5, 1.5, 3.0)), "blobs2d": ((7, 7), (1.5, 1.5))}
+
+
+def set_template(pl, P, name, mode, dev):
+    """The workload's template on a plan: dense, or as its 1-D factors in the separable mode."""
+    import torch
+
+    import synth
+    if mode != "separable":
+        pl.set_psf(torch.from_numpy(P.H).to(dev))
+        return
+    if name not in SEPARABLE:
+        raise SystemExit("--mode separable: the %s template is not a product of 1-D factors" % name)
+    q, sigma = SEPARABLE[name]
+    pl.set_psf_factors([torch.from_numpy(h).to(dev) for h in synth.gaussian_factors(q, sigma)])
 
 
 def dist_env():
@@ -268,7 +287,7 @@ def separable_report(dev, stream, npts=1000):
     import synth
     from paper_1711_11224_gb300 import Plan
     P = synth.fil3d()
-    q, sigma = (15, 15, 11), (1.5, 1.5, 3.0)
+    q, sigma = SEPARABLE["fil3d"]
     hs = synth.gaussian_factors(q, sigma)
     H = np.multiply.outer(np.multiply.outer(hs[0].astype(np.float64), hs[1]), hs[2])
     rng = np.random.default_rng(0)
@@ -391,7 +410,7 @@ def run_kernels_only(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream()
     pl = Plan(P.m, P.p, mode=args.mode)
-    pl.set_psf(torch.from_numpy(P.H).to(dev))
+    set_template(pl, P, args.workload, args.mode, dev)
     X = torch.from_numpy(P.X_true).to(dev)
     R = torch.empty(P.Y.shape, device=dev, dtype=torch.float32)
     G = torch.empty(P.m, device=dev, dtype=torch.float32)
@@ -684,6 +703,9 @@ def main():
         run_reference(args)
     elif args.kernels_only:
         run_kernels_only(args)
+    elif args.mode == "separable":
+        raise SystemExit("--mode separable runs with --kernels-only; the default line reports the separable "
+                         "iteration on fil3d under 'separable'")
     elif args.workload == "batch64":
         run_batch(args)
     else:
