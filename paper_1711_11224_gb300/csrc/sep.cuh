@@ -241,10 +241,18 @@ __global__ void __launch_bounds__(kSepThreads) sep_rows_kernel(const SepPass P)
     const int64_t nrows = P.outer;
     const int64_t nseg = (P.kout + seg - 1) / seg;
     const int64_t ntask = ((nrows + rb - 1) / rb) * nseg;
+    // row strides for tasks of several rows (rows shorter than 256 * 7 samples); a task of one row
+    // (r = 0) may be longer than 2^31 samples
+    const int kin = rb > 1 ? (int)P.kin : 0, kout = rb > 1 ? (int)P.kout : 0;
     for (int64_t task = blockIdx.x; task < ntask; task += gridDim.x) {
         const int64_t row0 = (task / nseg) * rb;
         const int64_t s0 = (task % nseg) * seg;
         const int64_t t0 = s0 + P.o - (Q - 1);           // input sample of shared column 0
+        // 32-bit offsets from per-task bases (r * kin and r * kout stay far below 2^31)
+        const int rows = (int)(nrows - row0 < rb ? nrows - row0 : rb);
+        const int xlo = (int)(t0 < 0 ? -t0 : 0);                      // columns whose sample is in [0, kin)
+        const int xhi = (int)(P.kin - t0 < span ? P.kin - t0 : span);
+        const float* tin = in + row0 * P.kin + t0;
         for (int i0 = tid; i0 < rb * span; i0 += kSepThreads * kSepBatch) {
             float v[kSepBatch];
             int so[kSepBatch];
@@ -252,9 +260,8 @@ __global__ void __launch_bounds__(kSepThreads) sep_rows_kernel(const SepPass P)
             for (int u = 0; u < kSepBatch; u++) {
                 const int i = i0 + u * kSepThreads;
                 const int r = (int)fdiv((uint32_t)i, P.dspan), xcol = i - r * span;
-                const int64_t row = row0 + r, t = t0 + xcol;
                 so[u] = i < rb * span ? r * pitch + xcol : -1;
-                v[u] = (so[u] >= 0 && row < nrows && t >= 0 && t < P.kin) ? in[row * P.kin + t] : 0.f;
+                v[u] = (so[u] >= 0 && r < rows && xcol >= xlo && xcol < xhi) ? tin[r * kin + xcol] : 0.f;
             }
 #pragma unroll
             for (int u = 0; u < kSepBatch; u++)
@@ -280,25 +287,30 @@ __global__ void __launch_bounds__(kSepThreads) sep_rows_kernel(const SepPass P)
         __syncthreads();
         // coalesced along the row; the next task's staging touches s_in only, and its compute loop
         // writes s_out after the barrier that follows that staging
+        const int xout = (int)(P.kout - s0 < seg ? P.kout - s0 : seg);    // outputs of the segment in the row
+        const int64_t obase = row0 * P.kout + s0;
         for (int i0 = tid; i0 < rb * seg; i0 += kSepThreads * kSepBatch) {
-            int64_t idx[kSepBatch];
+            int off[kSepBatch];
             float v[kSepBatch];
             bool ok[kSepBatch];
 #pragma unroll
             for (int u = 0; u < kSepBatch; u++) {
                 const int i = i0 + u * kSepThreads;
                 const int r = (int)fdiv((uint32_t)i, P.dseg), xcol = i - r * seg;
-                const int64_t row = row0 + r, s = s0 + xcol;
-                ok[u] = i < rb * seg && row < nrows && s < P.kout;
-                idx[u] = row * P.kout + s;
+                ok[u] = i < rb * seg && r < rows && xcol < xout;
+                off[u] = r * kout + xcol;
                 v[u] = ok[u] ? s_out[i] : 0.f;
             }
             if (EPI) {
+                int64_t idx[kSepBatch];
+#pragma unroll
+                for (int u = 0; u < kSepBatch; u++) idx[u] = obase + off[u];
                 e.put_batch<kSepBatch, true>(idx, v, ok);
             } else {
+                float* o = e.out + obase;
 #pragma unroll
                 for (int u = 0; u < kSepBatch; u++)
-                    if (ok[u]) e.out[idx[u]] = v[u];
+                    if (ok[u]) o[off[u]] = v[u];
             }
         }
     }
