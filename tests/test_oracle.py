@@ -131,6 +131,27 @@ def test_separable_closed_form():
     np.testing.assert_allclose(Y, Yc, rtol=1e-12, atol=1e-14)
 
 
+def test_product_template_matrix_is_kronecker_product():
+    """For H = h1 x h2 x h3 the block-Toeplitz matrix of Property 1 is the Kronecker product of the 1-D
+    full-convolution matrices (built here column by column with np.convolve on unit vectors); this is
+    the identity the separable-template mode computes axis by axis.  Also checks the oracle's adjoint
+    against the transposed Kronecker product."""
+    rng = np.random.default_rng(11)
+    m, q = (4, 5, 3), (3, 5, 3)
+    hs = [rng.standard_normal(v) for v in q]
+
+    def conv_matrix(h, n):
+        return np.stack([np.convolve(np.eye(n)[i], h) for i in range(n)], axis=1)
+
+    K = np.kron(np.kron(conv_matrix(hs[0], m[0]), conv_matrix(hs[1], m[1])), conv_matrix(hs[2], m[2]))
+    H = np.einsum("i,j,k->ijk", *hs)
+    np.testing.assert_allclose(dense_A(H, m), K, rtol=0, atol=1e-13)
+    X = rng.standard_normal(m)
+    R = rng.standard_normal(tuple(a + b - 1 for a, b in zip(m, q)))
+    np.testing.assert_allclose(oracle.forward(X, H).ravel(), K @ X.ravel(), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(oracle.adjoint(R, H).ravel(), K.T @ R.ravel(), rtol=1e-12, atol=1e-12)
+
+
 def test_points_match_full():
     X, H, R = synth.random_case((13, 10, 17), (5, 7, 3), seed=8)
     Y = oracle.forward(X, H)
