@@ -35,7 +35,6 @@ constexpr int kSepThreads = 256;
 constexpr int kSepRowC = 7;       // outputs per thread of the rows kernel
 constexpr int kSepColC = 8;       // outputs per window step of the cols kernel
 constexpr int kSepBatch = 8;      // elements per thread whose loads are issued before any store
-static_assert(kSepColC % kSepBatch == 0, "window steps are whole epilogue batches");
 
 __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f)
 {
@@ -71,10 +70,9 @@ struct SepEpi {
     float f, m, a, xx, sy;
 
     // N outputs (ok[i] false: skipped): every load of the batch is issued before its first store, so a
-    // thread keeps N requests in flight instead of waiting on each in turn.  UPD: the projected-update
-    // role is compiled in (the rows kernel; the cols kernel never ends an adjoint, whose last pass runs
-    // along the contiguous axis).
-    template <int N, bool UPD>
+    // thread keeps N requests in flight instead of waiting on each in turn.  Used by the rows kernel,
+    // which ends every adjoint (the cols kernel writes its forward residual itself).
+    template <int N>
     __device__ __forceinline__ void put_batch(const int64_t (&idx)[N], const float (&v)[N], const bool (&ok)[N])
     {
         if (role == ROLE_PLAIN) {
@@ -96,7 +94,6 @@ struct SepEpi {
                 }
             return;
         }
-        if (!UPD) return;
         const bool need_old = !fresh || want_sy;
         float xo[N], xq[N], go[N];
 #pragma unroll
@@ -205,7 +202,7 @@ __device__ __forceinline__ void sep_update_only(const SepPass& P, SepEpi& e)
             ok[u] = idx[u] < n;
             v[u] = 0.f;
         }
-        e.put_batch<kSepBatch, true>(idx, v, ok);
+        e.put_batch<kSepBatch>(idx, v, ok);
     }
 }
 
@@ -305,7 +302,7 @@ __global__ void __launch_bounds__(kSepThreads) sep_rows_kernel(const SepPass P)
                 int64_t idx[kSepBatch];
 #pragma unroll
                 for (int u = 0; u < kSepBatch; u++) idx[u] = obase + off[u];
-                e.put_batch<kSepBatch, true>(idx, v, ok);
+                e.put_batch<kSepBatch>(idx, v, ok);
             } else {
                 float* o = e.out + obase;
 #pragma unroll
