@@ -148,14 +148,39 @@ def oracle_sample(P, planes):
     return {"seconds": dt, "gmac": mac / 1e9, "planes": m1, "threads": oracle.num_threads()}
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu), else the machine type."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.machine()
+
+
 def cpu_baseline(P, planes):
+    """The FP64 oracle on all host cores, and on one thread over a sixteenth of the slab."""
+    import oracle
     s = oracle_sample(P, planes)
     nxnh = float(np.prod(P.m)) * float(P.H.size)
     rate = s["gmac"] / s["seconds"]
+    threads = oracle.num_threads()
+    oracle.set_num_threads(1)
+    try:
+        s1 = oracle_sample(P, max(1, planes // 16))
+    finally:
+        oracle.set_num_threads(threads)
     return {"value": rate, "unit": "GMAC/s", "cores": s["threads"], "kind": "oracle",
-            "iters_per_s": rate * 1e9 / (2.0 * nxnh),
+            "iters_per_s": rate * 1e9 / (2.0 * nxnh), "cpu_model": cpu_model(),
             "sample": "FP64 oracle forward + residual + adjoint + update on planes [0, %d) of axis 1 "
-                      "(%.3g GMAC, %.1f s)" % (s["planes"], s["gmac"], s["seconds"])}
+                      "(%.3g GMAC, %.1f s)" % (s["planes"], s["gmac"], s["seconds"]),
+            "single_thread": {"value": s1["gmac"] / s1["seconds"], "unit": "GMAC/s", "cores": s1["threads"],
+                              "sample": "planes [0, %d) (%.3g GMAC, %.1f s)" % (s1["planes"], s1["gmac"],
+                                                                              s1["seconds"])}}
 
 
 # ---------------------------------------------------------------- clocks

@@ -36,7 +36,7 @@ _lib = None
 
 __all__ = [
     "build", "forward", "adjoint", "adjoint_crop", "forward_points", "adjoint_points",
-    "grad_psf", "iterate", "richardson_lucy", "lipschitz", "x0_crop", "num_threads",
+    "grad_psf", "iterate", "richardson_lucy", "lipschitz", "x0_crop", "num_threads", "set_num_threads",
     "gradient_eq6", "objective",
 ]
 
@@ -76,12 +76,19 @@ def _load():
             lib.orc_iterate.restype = i32
             lib.orc_richardson_lucy.argtypes = dims + [dp, dp, dp, i32]
             lib.orc_num_threads.restype = i32
+            lib.orc_set_num_threads.argtypes = [i32]
+            lib.orc_set_num_threads.restype = None
             _lib = lib
     return _lib
 
 
 def num_threads():
     return int(_load().orc_num_threads())
+
+
+def set_num_threads(n):
+    """Threads of later calls (for timing; every result is independent of it)."""
+    _load().orc_set_num_threads(int(n))
 
 
 def _d(a):

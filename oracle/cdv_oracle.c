@@ -33,6 +33,16 @@ int orc_num_threads(void)
 #endif
 }
 
+/* Threads of the following parallel regions (timing runs only; results do not depend on it). */
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /*
  * Forward operator, Property 1: y(s) = sum_k x(k) h(s - k)  (Eq. 1, Y^v = A X^v).
  * Written as the shift-and-add of the block-Toeplitz rows of A: output plane
