@@ -32,7 +32,12 @@ def _need(t, shape, name):
 
 
 class Plan:
-    """A plan for one size: m samples of X per axis, template half-widths p."""
+    """A plan for one size: m samples of X per axis, template half-widths p.
+
+    mode: "fp32" (FP32 FMA), "split3" (tensor cores, split-BF16x3: FP32 accuracy), "tf32", "bf16"
+    (tensor cores, lower accuracy), "separable" (template given by its 1-D factors through
+    set_psf_factors, one 1-D pass per axis) or "fft" (cuFFT comparator, not the paper's method).
+    """
 
     def __init__(self, m, p, mode="fp32"):
         self.lib = B.load()
