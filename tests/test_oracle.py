@@ -117,6 +117,26 @@ def test_commutativity_and_mass():
     assert abs(Y.sum() - Xr.astype(np.float64).sum() * Hr.astype(np.float64).sum()) < 1e-11 * Y.sum()
 
 
+def test_linearity_in_image_and_template():
+    """Both operators are bilinear: linear in the image for a fixed template and in the template for a
+    fixed image (Property 1 writes Y as A_n^h X with A_n^h built linearly from h)."""
+    rng = np.random.default_rng(12)
+    m, q = (6, 9, 11), (3, 5, 7)
+    X1, X2 = rng.standard_normal(m), rng.standard_normal(m)
+    H1, H2 = rng.standard_normal(q), rng.standard_normal(q)
+    R1, R2 = (rng.standard_normal(tuple(a + b - 1 for a, b in zip(m, q))) for _ in range(2))
+    a, b = 0.75, -1.5
+    tol = dict(rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(oracle.forward(a * X1 + b * X2, H1),
+                               a * oracle.forward(X1, H1) + b * oracle.forward(X2, H1), **tol)
+    np.testing.assert_allclose(oracle.forward(X1, a * H1 + b * H2),
+                               a * oracle.forward(X1, H1) + b * oracle.forward(X1, H2), **tol)
+    np.testing.assert_allclose(oracle.adjoint(a * R1 + b * R2, H1),
+                               a * oracle.adjoint(R1, H1) + b * oracle.adjoint(R2, H1), **tol)
+    np.testing.assert_allclose(oracle.adjoint(R1, a * H1 + b * H2),
+                               a * oracle.adjoint(R1, H1) + b * oracle.adjoint(R1, H2), **tol)
+
+
 def test_separable_closed_form():
     """Separable X and H: Y is the outer product of 1-D textbook convolutions."""
     rng = np.random.default_rng(4)
