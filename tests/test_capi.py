@@ -62,3 +62,31 @@ def test_iter_opts_defaults(lib):
     o = B.IterOpts()
     lib.cdv_iter_opts_default(ctypes.byref(o))
     assert (o.x0_policy, o.delta0, o.beta, o.max_halvings, o.max_rejects, o.use_graph) == (0, 0.0, 0.5, 20, 16, 1)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every field offset and size of the ctypes structures equals the C compiler's for include/cdv.h."""
+    import shutil
+    import subprocess
+    from paper_1711_11224_gb300 import _binding as B
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    structs = {"cdv_iter_opts": B.IterOpts, "cdv_iter_report": B.IterReport, "cdv_plan_info": B.PlanInfo}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "cdv.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f in cls._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f[0], cname, f[0]))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(root, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, cls in structs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
+        for f in cls._fields_:
+            assert got[(cname, f[0])] == getattr(cls, f[0]).offset, (cname, f[0])
