@@ -55,12 +55,68 @@ def measured_hbm():
         return 6800.0, "fallback"
 
 
+# Peaks measured in this process on the GPU (filled by measure_peaks): the library's FP32 FMA probe and a
+# cuBLAS TF32 GEMM burst.
+LIVE_PEAKS = {}
+
+
+def measure_peaks(stream):
+    """FP32 FMA rate (cdv_probe_fp32_fma, CUDA events, best of 3) and the TF32 dense GEMM burst rate
+    (torch.matmul on float32 with TF32 allowed, 8192^3, best of 5), in TFLOP/s."""
+    import ctypes
+
+    import torch
+
+    from paper_1711_11224_gb300 import _binding
+    lib = _binding.load()
+    blocks, threads, iters = SM_COUNT * 4, 512, 1 << 15
+    out = torch.empty(blocks * threads, device="cuda", dtype=torch.float32)
+    best = None
+    for _ in range(4):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _binding.check(lib.cdv_probe_fp32_fma(ctypes.c_void_p(out.data_ptr()), blocks, threads, iters,
+                                              ctypes.c_void_p(stream.cuda_stream)))
+        b.record(stream)
+        b.synchronize()
+        t = a.elapsed_time(b) / 1e3
+        best = t if best is None else min(best, t)
+    LIVE_PEAKS["fp32_ffma"] = 16.0 * iters * blocks * threads / best / 1e12
+    n = 8192
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        A = torch.randn(n, n, device="cuda")
+        B = torch.randn(n, n, device="cuda")
+        C = torch.empty(n, n, device="cuda")
+        torch.matmul(A, B, out=C)
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(5):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            torch.matmul(A, B, out=C)
+            b.record(stream)
+            b.synchronize()
+            t = a.elapsed_time(b) / 1e3
+            best = t if best is None else min(best, t)
+        LIVE_PEAKS["tf32_gemm"] = 2.0 * n ** 3 / best / 1e12
+        del A, B, C
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    return dict(LIVE_PEAKS)
+
+
 def roofline_peak(mode):
     """(bound, peak TFLOP/s, basis) for the convolution kernels of a form (not the FFT comparator)."""
     if mode == "fp32":
-        return "alu", FP32_PEAK_TFLOPS, "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (FFMA)"
+        return "alu", FP32_PEAK_TFLOPS, "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (FFMA, nominal)"
     bf16, src = measured_peaks()
     if mode == "tf32":
+        if "tf32_gemm" in LIVE_PEAKS:
+            return "tensor", LIVE_PEAKS["tf32_gemm"], "cuBLAS TF32 dense GEMM burst (8192^3) measured in this run"
         return "tensor", bf16 * 1.1 / 2.25, "TF32 dense = %s BF16 peak %.1f x nominal ratio 1.1/2.25" % (src, bf16)
     return "tensor", bf16, "%s BF16 dense peak (cuBLAS burst)" % src
 
@@ -69,6 +125,7 @@ WORKLOADS = {
     "ring3d": "X 512x512x128 filaments (320), H 31x31x21 Gaussian-plus-ring, Y = X (*) H + Poisson noise",
     "fil3d": "X 256x256x64 filaments (40) + background 10, H 15x15x11 Gaussian sigma (1.5,1.5,3), Poisson noise",
     "blobs2d": "X 64x64 Gaussian blobs (20), H 7x7 Gaussian sigma 1.5, Gaussian noise 0.01",
+    "grad3d": "4 filament volumes 128x128x64, H 11x11x9 Gaussian sigma (1.5,1.5,3): forward, dX and dH",
     "batch64": "64 filament volumes, sizes U[32,256]^2 x U[16,128], odd templates U[5,21] per axis, "
                "Gaussian sigma U[0.8,4], Poisson noise; solved together (batched solver)",
 }
@@ -94,6 +151,9 @@ def parse():
                          "(the same kernels; for profilers that do not follow conditional graph nodes)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample-planes", type=int, default=96)
+    ap.add_argument("--forms-iter", default=None, metavar="REF.npz",
+                    help="run every form's K-step iteration and compare it with the FP64 oracle's result in "
+                         "REF.npz (written by oracle/make_refs.py)")
     ap.add_argument("--kernels-only", action="store_true",
                     help="time the forward and adjoint kernels alone (launch order: forward, adjoint, forward, adjoint)")
     return ap.parse_args()
@@ -256,6 +316,64 @@ def traffic_record(workload, mode, kernel):
         return float(e["bytes_per_launch"])
     except Exception:
         return None
+
+
+def kernel_hashes():
+    """Source hashes of the two convolution engines, as forms_iter records them."""
+    return {"fp32": kernel_hash("fp32"), "tc": kernel_hash("split3")}
+
+
+def forms_iter_record(workload):
+    """The full-size 100-step comparison of every form with the FP64 oracle (bench.py --forms-iter), if it
+    was recorded for the kernels as they are now; None otherwise."""
+    path = os.path.join(ROOT, "profiles", "forms_iter_%s.json" % workload)
+    try:
+        rec = json.load(open(path))
+    except Exception:
+        return None
+    if rec.get("kernel_hashes") != kernel_hashes():
+        return None
+    rec["source"] = "recorded by bench.py --forms-iter (profiles/forms_iter_%s.json)" % workload
+    return rec
+
+
+def run_forms_iter(args):
+    """Every form's K-step iteration on the workload against the FP64 oracle's K steps from the same start
+    (the centre crop of Y), read from the file that oracle/make_refs.py wrote (its input hash is checked):
+    relative L2 of x_K, the largest relative error of f_0..f_K, accepted and rejected trials."""
+    import importlib.util
+
+    import torch
+
+    from paper_1711_11224_gb300 import Plan
+    spec = importlib.util.spec_from_file_location("make_refs", os.path.join(ROOT, "oracle", "make_refs.py"))
+    mr = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mr)
+    P = problem(args.workload)
+    ref = np.load(args.forms_iter)
+    if str(ref["input_sha256"]) != mr.input_sha256(P):
+        raise SystemExit("--forms-iter: %s was computed from other inputs" % args.forms_iter)
+    K = int(P.K)
+    Xr = ref["X"].astype(np.float64)
+    fr = ref["f"]
+    dev = torch.device("cuda", 0)
+    Y = torch.from_numpy(P.Y).to(dev)
+    res = {"workload": "%s: %s" % (args.workload, WORKLOADS[args.workload]), "K": K,
+           "reference": {"accepted": int(ref["accepted"]), "rejected": int(ref["rejected"]),
+                         "seconds": float(ref["seconds"]), "threads": int(ref["threads"]),
+                         "stored": "float32-rounded FP64 iterate (6e-8 relative at most)"},
+           "kernel_hashes": kernel_hashes(), "forms": {}}
+    for mode in ("fp32", "split3", "tf32", "bf16", "fft"):
+        with Plan(P.m, P.p, mode=mode) as pl:
+            pl.set_psf(torch.from_numpy(P.H).to(dev))
+            X, rep = pl.iterate(Y, K=K, x0="crop", max_rejects=64)
+            Xg = X.cpu().numpy().astype(np.float64)
+        n = min(rep["accepted"], K) + 1
+        res["forms"][mode] = {"rel_l2_x": float(np.linalg.norm(Xg - Xr) / np.linalg.norm(Xr)),
+                              "max_rel_err_f": float(np.max(np.abs(rep["f"][:n] - fr[:n]) / fr[:n])),
+                              "accepted": rep["accepted"], "rejected": rep["rejected"], "status": rep["status"]}
+        print(json.dumps({mode: res["forms"][mode]}), flush=True)
+    print(json.dumps(res), flush=True)
 
 
 def forms_report(P, dev, stream, npts=1000):
@@ -455,6 +573,111 @@ def run_kernels_only(args):
     print(json.dumps({"workload": args.workload, "forward_ms": tf * 1e3, "adjoint_ms": ta * 1e3,
                       "forward_tflops": flops / tf / 1e12, "adjoint_tflops": flops / ta / 1e12}), flush=True)
     pl.close()
+
+
+def run_grad(args):
+    """Differentiation workload: Y = X (*) H for a batch of 4 volumes, then the backward pass
+    dX = A^T dY (the adjoint kernel) and dH = sum_b sum_k X_b(k) dY_b(k + j) (the template-gradient
+    kernel), as ConvFn runs them.  A step is forward + dX + dH for the whole batch; GMAC counts all three
+    (each B x prod(m) x prod(2p+1) multiply-adds).  The FP64 oracle does the same on the host cores."""
+    import torch
+
+    import oracle
+    import synth
+    from paper_1711_11224_gb300 import Plan
+    from paper_1711_11224_gb300.autograd import conv
+    Xs, H, sigma = synth.grad3d()
+    B = Xs.shape[0]
+    m = Xs.shape[1:]
+    p = tuple((q - 1) // 2 for q in H.shape)
+    ny = tuple(a + 2 * b for a, b in zip(m, p))
+    rng = np.random.default_rng(0)
+    dYh = rng.standard_normal((B,) + ny).astype(np.float32)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    X = torch.from_numpy(Xs).to(dev)
+    dY = torch.from_numpy(dYh).to(dev)
+    Hd = torch.from_numpy(H).to(dev)
+    pl = Plan(m, p)
+    pl.set_psf(Hd)
+    Y = torch.empty((B,) + ny, device=dev)
+    dX = torch.empty_like(X)
+    dH = torch.empty(H.shape, device=dev)
+
+    def step():
+        pl.forward(X, Y)
+        pl.adjoint(dY, dX)
+        pl.grad_psf(X, dY, dH)
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    K = args.steps
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(0) as clk:
+        ev0.record(stream)
+        for _ in range(K):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    t = ev0.elapsed_time(ev1) / 1e3
+    macs = float(B) * float(np.prod(m)) * float(H.size)
+    tf = time_kernel(lambda: pl.forward(X, Y), stream, reps=5)
+    ta = time_kernel(lambda: pl.adjoint(dY, dX), stream, reps=5)
+    tg = time_kernel(lambda: pl.grad_psf(X, dY, dH), stream, reps=5)
+    pl.sync()
+    # accuracy of the three results against the FP64 oracle (same inputs)
+    t0 = time.perf_counter()
+    yo = np.stack([oracle.forward(Xs[b], H) for b in range(B)])
+    dxo = np.stack([oracle.adjoint(dYh[b], H) for b in range(B)])
+    dho = oracle.grad_psf(Xs, dYh, H.shape)
+    tor = time.perf_counter() - t0
+    rel = lambda a, b: float(np.linalg.norm(a.astype(np.float64) - b) / np.linalg.norm(b))
+    err = {"forward": rel(Y.cpu().numpy(), yo), "dX": rel(dX.cpu().numpy(), dxo), "dH": rel(dH.cpu().numpy(), dho)}
+    peaks = measure_peaks(stream)
+    fl = 2.0 * macs
+    out = {"metric": "GMAC/s of the differentiable convolution (forward + dX + dH per batch)", "value": 3 * macs * K / t / 1e9,
+           "unit": "GMAC/s", "n_gpus": 1, "steps": K, "warmup": max(3, args.warmup), "ms_per_step": t * 1e3 / K,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "grad3d: 4 filament volumes 128x128x64 (10 filaments each), H 11x11x9 Gaussian "
+                                  "sigma (1.5, 1.5, 3), dY standard normal (seeded)",
+                      "step": "forward (batch 4) + adjoint dX (batch 4) + template gradient dH",
+                      "l2": "inputs %.0f MB + %.0f MB (X, dY), below L2 between steps" % (Xs.nbytes / 1e6, dYh.nbytes / 1e6)},
+           "kernels_ms": {"forward": tf * 1e3, "dX": ta * 1e3, "dH": tg * 1e3},
+           "roofline": {"bound": "alu", "kernel": "grad_psf_kernel (dH)", "achieved": fl / tg / 1e12,
+                        "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": fl / tg / 1e12 / FP32_PEAK_TFLOPS,
+                        "frac_of_measured_ffma": fl / tg / 1e12 / peaks["fp32_ffma"], "traffic": None,
+                        "forward_frac": fl / tf / 1e12 / FP32_PEAK_TFLOPS, "dX_frac": fl / ta / 1e12 / FP32_PEAK_TFLOPS,
+                        "achieved_is": "2 x B x prod(m) x prod(2p+1) flop / kernel time (CUDA events)"},
+           "rel_l2_vs_oracle": err, "gpu_launches": K * 4, "clocks": clk.summary(),
+           "cpu_baseline": {"value": 3 * macs / tor / 1e9, "unit": "GMAC/s", "cores": oracle.num_threads(),
+                            "kind": "oracle", "sample": "the whole batch: FP64 oracle forward, adjoint and grad_psf "
+                                                        "(%.1f s)" % tor},
+           "measured_peaks": peaks}
+    # end to end through the public autograd API: X from pinned host memory, loss and dH back
+    Xh = torch.empty(X.shape, dtype=torch.float32, pin_memory=True)
+    Xh.copy_(torch.from_numpy(Xs))
+    W = dY
+
+    def e2e_step():
+        Xd = Xh.to(dev, non_blocking=True).requires_grad_(True)
+        Hg = Hd.clone().requires_grad_(True)
+        loss = (conv(Xd, Hg) * W).sum()
+        loss.backward()
+        return float(loss.item()), Hg.grad.cpu()
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        e2e_step()
+    te = time.perf_counter() - t0
+    out["e2e"] = {"value": 3 * macs * K / te / 1e9, "unit": "GMAC/s", "h2d_bytes_per_step": int(Xs.nbytes),
+                  "d2h_bytes_per_step": 8 + int(H.nbytes), "seconds": te,
+                  "call": "paper_1711_11224_gb300.conv (ConvFn) forward + loss.backward(): X copied in, the loss "
+                          "and dH copied out every step"}
+    pl.close()
+    print(json.dumps(out), flush=True)
 
 
 def run_batch(args):
@@ -657,8 +880,19 @@ def run_cdv(args):
         out["roofline"]["tile"] = {"cols_per_plane": info["cols"][d], "K": info["K"][d], "grid": info["grid"][d],
                                    "tiles": info["tiles"][d]}
     out["clocks"] = clk.summary()
+    if rank == 0:
+        peaks = measure_peaks(stream)
+        out["measured_peaks"] = {"fp32_ffma_tflops": peaks["fp32_ffma"], "tf32_gemm_tflops": peaks["tf32_gemm"],
+                                 "how": "cdv_probe_fp32_fma (8 FMA chains per thread, 608 x 512 threads) and "
+                                        "cuBLAS TF32 8192^3 GEMM, CUDA events, best of several, after the "
+                                        "timed region"}
+        if args.mode == "fp32":
+            out["roofline"]["frac_of_measured_ffma"] = achieved / peaks["fp32_ffma"]
     if rank == 0 and not args.no_forms:
         out["forms"] = forms_report(P, dev, stream)
+        rec = forms_iter_record(args.workload)
+        if rec is not None:
+            out["forms_iter"] = rec
 
     # end to end through the host-array C-ABI call (pinned buffers, copies inside the clock)
     if not args.no_e2e:
@@ -678,8 +912,11 @@ def run_cdv(args):
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             te = float(tt.item())
         out["e2e"] = {"value": rep2["gmac"] * ws / te, "unit": "GMAC/s",
-                      "h2d_bytes_per_step": int(P.Y.nbytes), "d2h_bytes_per_step": int(P.X_true.nbytes),
-                      "seconds": te, "call": "cdv_iterate_host (x0 = centre crop of Y; K steps per call)"}
+                      "h2d_bytes_per_step": int(P.Y.nbytes) / K, "d2h_bytes_per_step": int(P.X_true.nbytes) / K,
+                      "h2d_bytes_per_call": int(P.Y.nbytes), "d2h_bytes_per_call": int(P.X_true.nbytes),
+                      "steps_per_call": K, "seconds": te,
+                      "call": "cdv_iterate_host (x0 = centre crop of Y; K steps per call: Y copied in and x_K "
+                              "copied out once per call, so the per-step bytes are the per-call bytes / K)"}
     if rank == 0 and not args.no_cpu and ws == 1:
         out["cpu_baseline"] = cpu_baseline(P, args.cpu_sample_planes)
     if rank == 0 and not args.no_forms:
@@ -726,6 +963,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.forms_iter:
+        run_forms_iter(args)
     elif args.kernels_only:
         run_kernels_only(args)
     elif args.mode == "separable":
@@ -733,6 +972,8 @@ def main():
                          "iteration on fil3d under 'separable'")
     elif args.workload == "batch64":
         run_batch(args)
+    elif args.workload == "grad3d":
+        run_grad(args)
     else:
         run_cdv(args)
 

@@ -184,8 +184,11 @@ cdv_status cdv_grad_psf(cdv_plan* plan, int batch, const float* X, const float* 
  * cdv_plan_create; X, dY and dH are as in cdv_grad_psf and owned by the
  * caller.  The call allocates nothing.  Its FP64 partials live in a
  * library-wide static device array of 4 MiB (held by every GPU that loads
- * the library, until exit), so the template may have at most 524288 samples
- * (larger: CDV_ERR_UNSUPPORTED, nothing enqueued).  The first call on each
+ * the library, until exit), so the template may have at most 524288 samples;
+ * one block stages 16 + 2 p2 template rows of about 72 + 2 p3 floats and its
+ * shared memory may not exceed 227 KB (roughly (16 + 2 p2) (72 + 2 p3) <=
+ * 55,000 floats for narrow rows), and q2 * ceil(q3 / 4) may not exceed 1024.
+ * Beyond any of these limits: CDV_ERR_UNSUPPORTED, nothing enqueued.  The first call on each
  * device looks up the array's address and must come before any stream
  * capture.  All calls share the array: calls that overlap on the GPU race,
  * so order them on one stream.  Asynchronous on `stream`.
@@ -314,8 +317,35 @@ cdv_status cdv_batch_iterate(cdv_batch* b, const float* const* Y, float* const* 
 /* Free everything the batch plan owns.  NULL is accepted. */
 cdv_status cdv_batch_destroy(cdv_batch* b);
 
-/* Wait for `stream`, then return and clear the plan's device status word. */
+/* Wait for `stream`, then return and clear the plan's device status word.
+ * A report filled by cdv_iterate also returns that word (as its status) and
+ * clears it. */
 cdv_status cdv_plan_sync_status(cdv_plan* plan, void* stream);
+
+/*
+ * Budget, in SM clock cycles, of every barrier wait in the work loops of the
+ * tensor-core kernels of this plan (0: the default, 1e9 cycles, about 0.5 s).
+ * A wait that runs out records CDV_ERR_TIMEOUT in the device status word; the
+ * block then stops issuing work, waits for its own copies and tensor-core
+ * operations (with a fixed budget of 2e9 cycles), frees its tensor memory and
+ * exits, and later launches of the plan skip their work until the word is
+ * read and cleared (cdv_plan_sync_status or a cdv_iterate report).  The paper
+ * has no counterpart: this bounds the kernels' spin waits.  Takes effect at
+ * the next launch; a captured iteration graph is re-captured.  Negative
+ * cycles: CDV_ERR_INVALID_ARG.  Other modes have no such waits and ignore it.
+ */
+cdv_status cdv_plan_set_wait_cycles(cdv_plan* plan, long long cycles);
+
+/*
+ * Measurement aid (the paper has no counterpart): `blocks` x `threads`
+ * threads each run 8 independent FP32 fused multiply-add chains for `iters`
+ * rounds, i.e. 16 * iters * blocks * threads flop, and write one float each
+ * to out[0 .. blocks*threads) (device, caller-owned).  Timed by the caller,
+ * this gives the GPU's FP32 FMA rate.  threads: a multiple of 32 up to 512;
+ * other arguments out of range: CDV_ERR_INVALID_ARG.  Asynchronous on
+ * `stream`.
+ */
+cdv_status cdv_probe_fp32_fma(float* out, int blocks, int threads, int iters, void* stream);
 
 #ifdef __cplusplus
 }

@@ -200,6 +200,7 @@ static bool tc_config(const cdv_plan* P, const ConvGeom& g, bool fwd, TcArgs& t)
     t.tmem_cols = 512;                      // 2 partial buffers x 2 M tiles x 128 columns
     t.sh_pitch = fwd ? P->pitch_r : P->pitch_x;
     t.err = P->dev_err;
+    t.wait_cycles = kTcWaitCycles;
     // deepest template-tile ring that fits: each stage is one template row of one input plane
     t.na = 2;
     t.ns = 16;
@@ -763,6 +764,7 @@ static cdv_status fill_report(cdv_plan* P, int K, cdv_iter_report* rep, cudaStre
     rep->accepted = st.accepted;
     rep->rejected = st.rejected;
     rep->status = derr ? derr : st.status;
+    if (derr) CDV_CUDA(cudaMemset(P->dev_err, 0, sizeof(int)), "clear error word");   // reported here
     rep->trials = st.trials;
     double f0 = 0.0;
     CDV_CUDA(cudaMemcpy(&f0, P->f_hist, sizeof(double), cudaMemcpyDeviceToHost), "read f0");
@@ -905,6 +907,17 @@ cdv_status cdv_richardson_lucy(cdv_plan* plan, const float* Y, float* X, int K, 
         CDV_CUDA(conv_fp32_launch(F, plan->tf, s), "RL forward");
         CDV_CUDA(conv_fp32_launch(A, plan->ta, s), "RL adjoint");
     }
+    return CDV_OK;
+}
+
+cdv_status cdv_plan_set_wait_cycles(cdv_plan* plan, long long cycles)
+{
+    if (!plan) return fail(CDV_ERR_INVALID_ARG, "plan is NULL");
+    if (cycles < 0) return fail(CDV_ERR_INVALID_ARG, "cycles = %lld", cycles);
+    const long long c = cycles == 0 ? kTcWaitCycles : cycles;
+    plan->tcf.wait_cycles = c;
+    plan->tca.wait_cycles = c;
+    plan->key_valid = false;               // a captured graph holds the old launch parameters
     return CDV_OK;
 }
 

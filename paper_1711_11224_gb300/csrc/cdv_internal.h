@@ -153,6 +153,10 @@ struct GradPsfPlan {
     int batch;
     int chunks;          // slabs of axis 1 reduced separately
 };
+// Dynamic shared memory of one grad_psf_kernel block for this plan (0: more than 1024 threads);
+// launches above kGradPsfMaxSmem fail with cudaErrorInvalidConfiguration.
+constexpr size_t kGradPsfMaxSmem = 227 * 1024;
+size_t grad_psf_smem_bytes(const GradPsfPlan& g);
 size_t grad_psf_partials(const GradPsfPlan& g);
 cudaError_t launch_grad_psf(const GradPsfPlan& g, const float* X, const float* dY, double* partial,
                             float* dH, cudaStream_t s);
@@ -201,8 +205,10 @@ struct TcArgs {
     void* sh_out_hi[2];
     void* sh_out_lo[2];
     int* err;            // device error word
+    long long wait_cycles;   // budget of each barrier wait in the work loops (clock64 cycles)
     IterCtx ctx;
 };
+constexpr long long kTcWaitCycles = 1000000000ll;   // default budget, about 0.5 s
 size_t tc_smem_bytes(const TcArgs& t);
 cudaError_t tc_prepare(int kind);
 cudaError_t tc_launch(const TcArgs& t, const struct CUtensorMap_st* maps, cudaStream_t s);

@@ -52,7 +52,7 @@
 //               FP32 engine plus the BF16/TF32 shadows the next convolution
 //               reads, stored through a per-warp staging tile so that warp
 //               accesses cover rows of 8 consecutive columns.
-// Every wait is bounded (about 0.5 s).  A wait that runs out records
+// Every wait is bounded (the plan's budget, about 0.5 s by default).  A wait that runs out records
 // CDV_ERR_TIMEOUT in the device error word; the CTA stops issuing work, waits
 // for its own copies and MMAs, frees its TMEM and exits.  CTAs that start
 // after an error has been recorded skip their work.
@@ -92,7 +92,9 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
 }
-// Bounded wait for the phase of the given parity; false after ~1e9 cycles (~0.5 s).
+// Bounded wait for the phase of the given parity; false after `budget` cycles (the work loops use the
+// plan's budget, 1e9 cycles or about 0.5 s by default; the drain before exit always kDrainCycles).
+constexpr long long kDrainCycles = 2000000000ll;
 __device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity)
 {
     unsigned ok;
@@ -102,13 +104,26 @@ __device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity)
                  : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity)
+// Non-blocking probe of the phase (try_wait may suspend the thread until the phase completes).
+__device__ __forceinline__ bool mbar_test(unsigned bar, unsigned parity)
 {
-    if (mbar_try(bar, parity)) return true;                        // fast path: no clock reads
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+// Budgets below this are probed without suspending, so the clock alone decides when they run out.
+constexpr long long kPollBelow = 1000000ll;
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, long long budget = kDrainCycles)
+{
+    const bool poll = budget < kPollBelow;
+    if (poll ? mbar_test(bar, parity) : mbar_try(bar, parity)) return true;   // fast path: no clock reads
     const long long t0 = clock64();
     for (;;) {
-        if (mbar_try(bar, parity)) return true;
-        if (clock64() - t0 > 1000000000ll) return false;
+        if (poll ? mbar_test(bar, parity) : mbar_try(bar, parity)) return true;
+        if (clock64() - t0 > budget) return false;
     }
 }
 __device__ __forceinline__ void tma3(unsigned dst, const CUtensorMap* map, int x, int y, int z, unsigned bar)
@@ -376,7 +391,7 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
             const int64_t v0 = C.S2 + G.o2 - (G.q2 - 1);            // input row of staged row 0
             for (int64_t u = C.ulo; u <= C.uhi && !*sflag; ++u, ++it) {
                 const int ab = it % T.na;
-                if (!mbar_wait(A_EMPTY(ab), (unsigned)(((it / T.na) & 1) ^ 1))) { fail(); break; }
+                if (!mbar_wait(A_EMPTY(ab), (unsigned)(((it / T.na) & 1) ^ 1), T.wait_cycles)) { fail(); break; }
                 mbar_expect_tx(A_FULL(ab), (unsigned)(NPREC * lay.a_bytes));
                 a_uses[ab] = it / T.na + 1;
                 for (int p = 0; p < NPREC; p++) {
@@ -393,7 +408,7 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
                 const int64_t j1lo = C.S1 + ilo + G.o1 - u;
                 const int nv = ihi - ilo + 1;
                 for (int j2 = 0; j2 < G.q2; j2++) {
-                    if (!mbar_wait(B_EMPTY(bs), bph ^ 1)) { fail(); break; }
+                    if (!mbar_wait(B_EMPTY(bs), bph ^ 1, T.wait_cycles)) { fail(); break; }
                     mbar_expect_tx(B_FULL(bs), (unsigned)(NPREC * T.kchunks * nv * W * 16));
                     for (int p = 0; p < NPREC; p++) {
                         const unsigned char* src0 = reinterpret_cast<const unsigned char*>(T.bt[p]);
@@ -439,8 +454,8 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
             for (int64_t u = C.ulo; u <= C.uhi; ++u, ++it) {
                 const int b = it & 1;
                 const int ab = it % T.na;
-                bool w = it < 2 || mbar_wait(ACC_FREE(b), (unsigned)(((it >> 1) - 1) & 1));
-                w = w && mbar_wait(A_FULL(ab), (unsigned)((it / T.na) & 1));
+                bool w = it < 2 || mbar_wait(ACC_FREE(b), (unsigned)(((it >> 1) - 1) & 1), T.wait_cycles);
+                w = w && mbar_wait(A_FULL(ab), (unsigned)((it / T.na) & 1), T.wait_cycles);
                 if (!__all_sync(0xffffffffu, w && !*sflag)) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 int ilo, ihi, lo, hi;
@@ -455,7 +470,7 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
                 const unsigned a_lo = a_hi + (unsigned)(NPREC - 1) * a_part16;
                 unsigned acc = 0;                                          // fresh partial per input plane
                 for (int j2 = 0; j2 < G.q2; j2++) {
-                    if (!__all_sync(0xffffffffu, mbar_wait(B_FULL(bs), bph))) { ok = false; break; }
+                    if (!__all_sync(0xffffffffu, mbar_wait(B_FULL(bs), bph, T.wait_cycles))) { ok = false; break; }
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                     const unsigned b_hi = sB16 + (unsigned)(bs * NPREC) * b_part16;
                     const uint64_t bh = db0 + b_hi, bl = db0 + b_hi + (unsigned)(NPREC - 1) * b_part16;
@@ -506,7 +521,7 @@ conv_tc_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtenso
             if (run) {
                 for (int64_t u = C.ulo; u <= C.uhi; ++u, ++it) {
                     const int b = it & 1;
-                    bool w = mbar_wait(ACC_FULL(b), (unsigned)((it >> 1) & 1));
+                    bool w = mbar_wait(ACC_FULL(b), (unsigned)((it >> 1) & 1), T.wait_cycles);
                     w = __all_sync(0xffffffffu, w && !*sflag);
                     if (!w) {
                         ok = false;

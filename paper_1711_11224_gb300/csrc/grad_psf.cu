@@ -150,19 +150,26 @@ __global__ void grad_psf_final_kernel(GradPsfPlan g, const double* partial, floa
 
 cudaError_t grad_psf_prepare()
 {
-    return cudaFuncSetAttribute(grad_psf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    return cudaFuncSetAttribute(grad_psf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGradPsfMaxSmem);
+}
+
+size_t grad_psf_smem_bytes(const GradPsfPlan& g)
+{
+    const GLayout l = GLayout::make(g);
+    if (l.threads > 1024) return 0;
+    const int threads = (l.threads + 31) & ~31;
+    size_t fl = (size_t)KC * KW + (size_t)l.drows * l.dpitch;
+    fl = (fl + 1) & ~(size_t)1;
+    return fl * sizeof(float) + (size_t)threads * RJ * sizeof(double);
 }
 
 cudaError_t launch_grad_psf(const GradPsfPlan& g, const float* X, const float* dY, double* partial, float* dH,
                             cudaStream_t s)
 {
     const GLayout l = GLayout::make(g);
-    if (l.threads > 1024) return cudaErrorInvalidConfiguration;
+    const size_t smem = grad_psf_smem_bytes(g);
+    if (smem == 0 || smem > kGradPsfMaxSmem) return cudaErrorInvalidConfiguration;
     const int threads = (l.threads + 31) & ~31;
-    size_t fl = (size_t)KC * KW + (size_t)l.drows * l.dpitch;
-    fl = (fl + 1) & ~(size_t)1;
-    const size_t smem = fl * sizeof(float) + (size_t)threads * RJ * sizeof(double);
-    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
     grad_psf_kernel<<<g.q1 * g.chunks, threads, smem, s>>>(g, l, X, dY, partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -95,10 +95,14 @@ extern "C" cdv_status cdv_grad_psf_static(int n, const int64_t* m, const int32_t
         return fail(CDV_ERR_UNSUPPORTED, "template rows too wide for one block (q2 = %d, q3 = %d)", q2, q3);
     int chunks = std::max(1, (152 * 4 + q1 - 1) / q1);
     chunks = (int)std::min<size_t>((size_t)chunks, kScratchDoubles / nh);
+    cdv::GradPsfPlan g{mm[0], mm[1], mm[2], q1, q2, q3, batch, chunks};
+    const size_t smem = cdv::grad_psf_smem_bytes(g);
+    if (smem == 0 || smem > cdv::kGradPsfMaxSmem)
+        return fail(CDV_ERR_UNSUPPORTED, "template rows need %zu bytes of shared memory per block (at most %zu)",
+                    smem, cdv::kGradPsfMaxSmem);
     double* scratch = nullptr;
     cdv_status st = scratch_for_current_device(&scratch);
     if (st != CDV_OK) return st;
-    cdv::GradPsfPlan g{mm[0], mm[1], mm[2], q1, q2, q3, batch, chunks};
     cudaError_t e = cdv::launch_grad_psf(g, X, dY, scratch, dH, (cudaStream_t)stream);
     if (e != cudaSuccess) return fail(CDV_ERR_CUDA, "grad_psf (static scratch): %s", cudaGetErrorString(e));
     return CDV_OK;

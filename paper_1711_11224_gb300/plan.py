@@ -219,6 +219,11 @@ class Plan:
     def sync(self):
         B.check(self.lib.cdv_plan_sync_status(self._h, _stream()))
 
+    def set_wait_cycles(self, cycles=0):
+        """Budget of each barrier wait in the tensor-core kernels (clock cycles; 0: the default)."""
+        B.check(self.lib.cdv_plan_set_wait_cycles(self._h, int(cycles)))
+        return self
+
 
 class BatchPlan:
     """Many independent problems iterated together (FP32): volume i has m[i] samples, half-widths p[i]."""

@@ -34,7 +34,7 @@ import numpy as np
 __all__ = [
     "Problem", "gaussian_psf", "gaussian_factors", "ring_psf", "blobs", "filaments", "observe",
     "blobs2d", "fil3d", "grad3d", "ring3d", "batch64", "batch64_shapes",
-    "scaled_fil3d", "integer_case", "random_case", "WORKLOADS",
+    "scaled_fil3d", "scaled_ring3d", "integer_case", "random_case", "WORKLOADS",
 ]
 
 
@@ -196,6 +196,17 @@ def ring3d(seed=0, K=100):
     H = ring_psf()
     Y = observe(X, H, r, noise="poisson")
     return Problem("ring3d", X, H, Y, K, {"noise": "poisson", "filaments": 320})
+
+
+def scaled_ring3d(shape, seed=0, K=100):
+    """Filament volume of any size at the ring3d density (320 per 512x512x128) with the full
+    31x31x21 Gaussian-plus-ring template and Poisson noise."""
+    n = max(1, int(round(320 * np.prod(shape) / (512 * 512 * 128))))
+    r = _rng(seed, 9)
+    X = filaments(shape, n, r)
+    H = ring_psf()
+    Y = observe(X, H, r, noise="poisson")
+    return Problem("ring3d_%s" % "x".join(map(str, shape)), X, H, Y, K, {"noise": "poisson", "filaments": n})
 
 
 def batch64_shapes(seed=0, count=64):

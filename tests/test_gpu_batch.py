@@ -81,15 +81,42 @@ def test_batch_graph_replay_and_repeat():
         np.testing.assert_array_equal(a, b)
 
 
-def test_batch64_workload_subset_equals_single():
+@pytest.fixture(scope="module")
+def batch64_run():
     """64 uneven volumes (sizes U[32,256]^2 x U[16,128], templates odd U[5,21]), 200 steps, one graph."""
     from paper_1711_11224_gb300 import BatchPlan
     probs = synth.batch64(K=200)
     with BatchPlan([P.m for P in probs], [P.p for P in probs]) as bp:
         bp.set_psfs([_dev(P.H) for P in probs])
         Xs, reps = bp.iterate([_dev(P.Y) for P in probs], K=200, x0="crop")
+        Xh = [X.cpu().numpy() for X in Xs]
+    return probs, Xh, reps
+
+
+def test_batch64_workload_subset_equals_single(batch64_run):
+    probs, Xs, reps = batch64_run
     assert all(r["status"] == "CDV_OK" and r["accepted"] == 200 for r in reps)
     assert all(np.all(np.diff(r["f"]) < 0) for r in reps)
     for i in (0, 17, 40, 63):
         Xs_, rs = _single(probs[i], 200)
-        np.testing.assert_array_equal(Xs[i].cpu().numpy(), Xs_)
+        np.testing.assert_array_equal(Xs[i], Xs_)
+
+
+# The cheapest volumes of the batch for the FP64 oracle, two of them with a 21-wide template axis
+# (volume 48: 48x86x32 with 7x21x15; volume 63: 65x72x61 with 15x7x21 along the contiguous axis).
+ORACLE_VOLUMES = (19, 13, 43, 48, 63)
+
+
+def test_batch64_volumes_match_oracle_200_steps(batch64_run):
+    """200 accepted steps of the batched solver against the oracle's 200 steps on the same volume."""
+    probs, Xs, reps = batch64_run
+    assert any(21 in probs[i].H.shape for i in ORACLE_VOLUMES)
+    assert probs[63].H.shape[2] == 21
+    for i in ORACLE_VOLUMES:
+        P = probs[i]
+        ref = oracle.iterate(P.Y, P.H, oracle.x0_crop(P.Y, P.p), 200)
+        assert ref["accepted"] == reps[i]["accepted"] == 200
+        e = rel_l2(Xs[i], ref["X"])
+        print("volume %d m=%s q=%s: x_200 rel-L2 %.3e" % (i, P.m, P.H.shape, e))
+        assert e <= TOL_ITER
+        np.testing.assert_allclose(reps[i]["f"], ref["f"], rtol=1e-5)

@@ -411,3 +411,36 @@ def test_bb_converges_to_nnls_in_fewer_steps():
     assert nb is not None and (npl is None or nb * 3 < npl)
     assert np.max(bb["delta"]) > oracle.lipschitz(H) ** -1 * 2       # longer steps than 1/L are taken
     np.testing.assert_allclose(bb["X"].ravel(), xs, atol=1e-4)
+
+
+def test_bb_lag_is_one_step_cauchy_length_two_steps_back():
+    """On a quadratic whose iterates stay positive (no projection), s = x_{k-1} - x_{k-2} equals
+    -delta_{k-2} grad f(x_{k-2}) and v = A^T A s, so the lagged Barzilai-Borwein length <s,s>/<s,v> of
+    step k is the exact line-search (Cauchy) length of the gradient two steps back,
+    |g|^2 / (g^T A^T A g) with g = grad f(x_{k-2}); an unlagged length would be that of grad f(x_{k-1}).
+    The Hessian here is not a multiple of the identity, so the two differ."""
+    rng = np.random.default_rng(16)
+    h = np.array([1.0, 0.1, 0.05])                   # A^T A well conditioned (kappa < 2): no rejections
+    m = 6
+    A = np.stack([np.convolve(np.eye(m)[i], h) for i in range(m)], axis=1)   # columns: library convolution
+    Q = A.T @ A
+    xt = 5.0 + rng.random(m)
+    y = A @ xt
+    x0 = xt + rng.uniform(-1.0, 1.0, m)
+    K = 8
+    out = oracle.iterate(y, h, x0, K=K, bb=True)
+    assert out["accepted"] == K and out["rejected"] == 0
+    d0 = 1.0 / np.sum(np.abs(h)) ** 2
+    grad = lambda x: A.T @ (A @ x - y)
+    xs = [x0]
+    for k in range(K):                               # replay with the oracle's step lengths
+        xs.append(np.maximum(xs[-1] - out["delta"][k] * grad(xs[-1]), 0.0))
+    assert min(x.min() for x in xs) > 0.0            # the projection never acts
+    np.testing.assert_allclose(xs[-1], out["X"], rtol=1e-12)
+    cauchy = lambda g: float(g @ g / (g @ Q @ g))
+    clamp = lambda d: min(max(d, d0), d0 * 2.0 ** 20)
+    np.testing.assert_allclose(out["delta"][:2], d0, rtol=1e-15)
+    lag1 = [clamp(cauchy(grad(xs[k - 2]))) for k in range(2, K)]
+    lag0 = [clamp(cauchy(grad(xs[k - 1]))) for k in range(2, K)]
+    np.testing.assert_allclose(out["delta"][2:], lag1, rtol=1e-9)
+    assert np.max(np.abs(np.array(lag0) / np.array(lag1) - 1.0)) > 1e-3
