@@ -3,6 +3,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -83,8 +84,10 @@ struct cdv_plan {
     TcArgs tcf{}, tca{};            // forward / adjoint launch templates
     void* xsh[2][2] = {};           // BF16/TF32 shadows of the iterates [buffer][part]
     void* rsh[2][2] = {};           // shadows of the residuals
-    int64_t pitch_x = 0, pitch_r = 0;
-    CUtensorMap map_x[4], map_r[4]; // hi0, lo0, hi1, lo1
+    void* xsh1[2][2] = {};          // narrow kernel: the same shifted right by 4 columns
+    void* rsh1[2][2] = {};
+    int64_t pitch_x = 0, pitch_r = 0, pitch_x1 = 0, pitch_r1 = 0;
+    CUtensorMap map_x[8], map_r[8]; // hi0, lo0, hi1, lo1 of copy 0, then of copy 1 (narrow kernel)
     int* dev_err = nullptr;
     bool tc() const { return mode == CDV_MODE_BF16 || mode == CDV_MODE_TF32 || mode == CDV_MODE_SPLIT_BF16X3; }
     bool fft() const { return mode == CDV_MODE_FFT; }
@@ -209,6 +212,70 @@ static bool tc_config(const cdv_plan* P, const ConvGeom& g, bool fwd, TcArgs& t)
     return tc_smem_bytes(t) <= 220 * 1024;
 }
 
+// Makespan of the wide kernel's persistent CTAs under the same MMA cost model, per 128-row M tile.
+static double tc_wide_makespan(const TcArgs& t)
+{
+    const ConvGeom& g = t.g;
+    std::vector<double> cta(std::max(1, t.grid), 0.0);
+    std::vector<double> plane_cost(t.tiles1, 0.0);
+    for (int t1 = 0; t1 < t.tiles1; t1++) {
+        const int64_t S1 = (int64_t)t1 * t.P, s1_end = std::min<int64_t>(S1 + t.P, g.b1);
+        const int64_t ulo = std::max<int64_t>(0, S1 + g.o1 - g.q1 + 1);
+        const int64_t uhi = std::min<int64_t>(g.a1 - 1, s1_end - 1 + g.o1);
+        for (int64_t u = ulo; u <= uhi; u++) {
+            const int64_t ilo = std::max<int64_t>(0, u - g.o1 - S1);
+            const int64_t ihi = std::min<int64_t>(s1_end - 1 - S1, u - g.o1 + g.q1 - 1 - S1);
+            int64_t nv = ihi - ilo + 1;
+            if (t.W == 8 && (nv & 1)) nv++;
+            plane_cost[t1] += std::max(46.0, t.W * nv / 2.0);
+        }
+    }
+    for (int tile = 0; tile < t.ntiles; tile++) {
+        const int t2 = (tile / t.tiles3) % t.tiles2, t1 = tile / (t.tiles3 * t.tiles2);
+        const int64_t nmt = std::min<int64_t>(t.MT, (g.b2 - (int64_t)t2 * 128 * t.MT + 127) / 128);
+        cta[tile % cta.size()] += plane_cost[t1] * g.q2 * (t.K / 16) * (double)nmt;
+    }
+    return *std::max_element(cta.begin(), cta.end());
+}
+
+// Narrow-kernel template of one direction from the wide one (shared fields), with pc output planes
+// per tile; false if the direction cannot run it (TF32, q1 > 31, windows not 4-column aligned, or
+// too little shared memory).
+static bool tc4_config(const cdv_plan* P, const TcArgs& wide, int pc, TcArgs& t)
+{
+    const ConvGeom& g = wide.g;
+    if (P->mode == CDV_MODE_TF32 || g.q1 > 31 || ((g.o3 - (g.q3 - 1)) % 4 + 4) % 4 != 0 || pc % 32 != 0 || pc < 32)
+        return false;
+    t = wide;
+    t.w4 = 1;
+    t.W = 4;
+    t.P = 0;
+    t.e = 0;
+    t.pc = pc;
+    t.kc = (g.q3 + 3 + 7) / 8;
+    t.K = 8 * t.kc;
+    t.kchunks = t.kc;
+    t.steps = (g.q2 * t.kc + 1) / 2;
+    t.spst = t.kc;
+    t.nst = (t.steps + t.spst - 1) / t.spst;
+    if (2 * t.rows + 1 >= (1 << 14)) return false;                 // descriptor offsets (16-byte units)
+    t.tiles1 = ceil_div(g.b1, pc);
+    t.tiles2 = ceil_div(g.b2, 128 * t.MT);
+    t.tiles3 = ceil_div(g.b3, 4);
+    const int64_t ntiles = (int64_t)t.tiles1 * t.tiles2 * t.tiles3;
+    if (ntiles > (1LL << 31) - 1) return false;
+    t.ntiles = (int)ntiles;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+        return false;
+    t.grid = (int)std::min<int64_t>(ntiles, nsm);
+    t.na = 2;
+    t.ns = 16;
+    while (tc4_smem_bytes(t) > 220 * 1024 && t.ns > 2) t.ns--;
+    return tc4_smem_bytes(t) <= 220 * 1024;
+}
+
 static cudaError_t make_map(CUtensorMap* m, const cdv_plan* P, void* base, int64_t d1, int64_t d2, int64_t d3,
                             int64_t pitch)
 {
@@ -236,6 +303,36 @@ static cudaError_t tc_setup(cdv_plan* P)
     P->pitch_x = (P->m[2] + 7) / 8 * 8;
     P->pitch_r = (P->gf.b3 + 7) / 8 * 8;
     if (!tc_config(P, P->gf, true, P->tcf) || !tc_config(P, P->ga, false, P->tca)) return cudaErrorNotSupported;
+    // The narrow kernel runs both directions or neither (each direction's epilogue writes the input
+    // shadows of the other); CDV_TC_KERNEL=wide|narrow overrides the cycle model.
+    {
+        const char* env = getenv("CDV_TC_KERNEL");
+        const bool force_wide = env && strcmp(env, "wide") == 0, force_narrow = env && strcmp(env, "narrow") == 0;
+        TcArgs best[2];
+        double cost[2] = {-1.0, -1.0};
+        for (int d = 0; d < 2; d++) {
+            const TcArgs& wide = d ? P->tca : P->tcf;
+            for (int pc = 32; pc <= 256; pc += 32) {
+                TcArgs c;
+                if (!tc4_config(P, wide, pc, c)) continue;
+                const double mk = tc4_model_cycles(c);
+                if (cost[d] < 0.0 || mk < cost[d]) {
+                    cost[d] = mk;
+                    best[d] = c;
+                }
+                if (c.tiles1 == 1) break;
+            }
+        }
+        const bool legal = cost[0] >= 0.0 && cost[1] >= 0.0;
+        const double wide_cost = tc_wide_makespan(P->tcf) + tc_wide_makespan(P->tca);
+        if (legal && !force_wide && (force_narrow || cost[0] + cost[1] < wide_cost)) {
+            P->tcf = best[0];
+            P->tca = best[1];
+        }
+    }
+    const bool w4 = P->tcf.w4 != 0;
+    P->pitch_x1 = (P->m[2] + 4 + 7) / 8 * 8;
+    P->pitch_r1 = (P->gf.b3 + 4 + 7) / 8 * 8;
     const size_t xs = (size_t)P->m[0] * P->m[1] * P->pitch_x * es;
     const size_t rs = (size_t)P->gf.b1 * P->gf.b2 * P->pitch_r * es;
     for (int b = 0; b < 2; b++)
@@ -248,10 +345,27 @@ static cudaError_t tc_setup(cdv_plan* P)
                 P->rsh[b][p] = P->rsh[b][0];
             }
         }
-    // Toeplitz tiles: per part, q2 x kchunks x (q1*W rows) x 16 bytes
+    if (w4) {
+        // shifted copies: columns 0-3 of every row stay zero (the window left of column 0)
+        const size_t xs1 = (size_t)P->m[0] * P->m[1] * P->pitch_x1 * es;
+        const size_t rs1 = (size_t)P->gf.b1 * P->gf.b2 * P->pitch_r1 * es;
+        for (int b = 0; b < 2; b++)
+            for (int p = 0; p < 2; p++) {
+                if (p < nprec) {
+                    if ((e = P->alloc((unsigned char**)&P->xsh1[b][p], xs1)) != cudaSuccess) return e;
+                    if ((e = P->alloc((unsigned char**)&P->rsh1[b][p], rs1)) != cudaSuccess) return e;
+                    if ((e = cudaMemset(P->xsh1[b][p], 0, xs1)) != cudaSuccess) return e;
+                    if ((e = cudaMemset(P->rsh1[b][p], 0, rs1)) != cudaSuccess) return e;
+                } else {
+                    P->xsh1[b][p] = P->xsh1[b][0];
+                    P->rsh1[b][p] = P->rsh1[b][0];
+                }
+            }
+    }
+    // Toeplitz tiles: per part, q2 x kchunks x (q1*W rows) x 16 bytes (narrow kernel: its stages)
     for (int d = 0; d < 2; d++) {
         TcArgs& t = d ? P->tca : P->tcf;
-        const size_t bytes = (size_t)P->q[1] * t.kchunks * P->q[0] * t.W * 16;
+        const size_t bytes = t.w4 ? tc4_btiles_bytes(t) : (size_t)P->q[1] * t.kchunks * P->q[0] * t.W * 16;
         for (int p = 0; p < 2; p++) {
             void* ptr = nullptr;
             if (p < nprec) {
@@ -269,13 +383,26 @@ static cudaError_t tc_setup(cdv_plan* P)
             if ((e = make_map(&P->map_r[2 * b + p], P, P->rsh[b][p], P->gf.b1, P->gf.b2, P->gf.b3, P->pitch_r)) !=
                 cudaSuccess)
                 return e;
+            if (!w4) continue;
+            if ((e = make_map(&P->map_x[4 + 2 * b + p], P, P->xsh1[b][p], P->m[0], P->m[1], P->m[2] + 4,
+                              P->pitch_x1)) != cudaSuccess)
+                return e;
+            if ((e = make_map(&P->map_r[4 + 2 * b + p], P, P->rsh1[b][p], P->gf.b1, P->gf.b2, P->gf.b3 + 4,
+                              P->pitch_r1)) != cudaSuccess)
+                return e;
         }
     for (int b = 0; b < 2; b++) {
         P->tcf.sh_out_hi[b] = P->rsh[b][0];
         P->tcf.sh_out_lo[b] = P->rsh[b][1];
         P->tca.sh_out_hi[b] = P->xsh[b][0];
         P->tca.sh_out_lo[b] = P->xsh[b][1];
+        P->tcf.sh_out_hi1[b] = P->rsh1[b][0];
+        P->tcf.sh_out_lo1[b] = P->rsh1[b][1];
+        P->tca.sh_out_hi1[b] = P->xsh1[b][0];
+        P->tca.sh_out_lo1[b] = P->xsh1[b][1];
     }
+    P->tcf.sh_pitch1 = P->pitch_r1;
+    P->tca.sh_pitch1 = P->pitch_x1;
     P->nparts = std::max(P->nparts, std::max(P->tcf.grid, P->tca.grid));
     return cudaSuccess;
 }
@@ -448,7 +575,12 @@ cdv_status cdv_plan_set_psf(cdv_plan* plan, const float* H, void* stream)
     CDV_CUDA(cudaMemcpyAsync(plan->H, H, plan->nh * sizeof(float), cudaMemcpyDeviceToDevice, s), "copy H");
     CDV_CUDA(launch_flip(plan->H, plan->Ht, plan->q[0], plan->q[1], plan->q[2], s), "flip H");
     CDV_CUDA(launch_abs_sum(plan->H, plan->nh, plan->absum, s), "sum |H|");
-    if (plan->tc()) {
+    if (plan->tc() && plan->tcf.w4) {
+        CDV_CUDA(tc4_build_btiles(plan->tcf, plan->H, const_cast<void*>(plan->tcf.bt[0]),
+                                  const_cast<void*>(plan->tcf.bt[1]), s), "Toeplitz stages (forward)");
+        CDV_CUDA(tc4_build_btiles(plan->tca, plan->Ht, const_cast<void*>(plan->tca.bt[0]),
+                                  const_cast<void*>(plan->tca.bt[1]), s), "Toeplitz stages (adjoint)");
+    } else if (plan->tc()) {
         const int q3 = plan->q[2];
         CDV_CUDA(tc_build_btiles(plan->H, plan->q[0], plan->q[1], q3, q3 - 1 + plan->tcf.e, plan->tcf.K, plan->tcf.W,
                                  (int)plan->mode, const_cast<void*>(plan->tcf.bt[0]),
@@ -540,7 +672,7 @@ cdv_status cdv_plan_describe(const cdv_plan* plan, cdv_plan_info* out)
             out->K[d] = t.K;
             out->grid[d] = t.grid;
             out->tiles[d] = t.ntiles;
-            out->executed_macs[d] = tc_executed_macs(t);
+            out->executed_macs[d] = t.w4 ? tc4_executed_macs(t) : tc_executed_macs(t);
         }
     }
     return CDV_OK;
@@ -584,6 +716,14 @@ static cdv_status run_conv(cdv_plan* P, bool fwd, int batch, const float* in, fl
             else
                 CDV_CUDA(tc_shadow(src, g.a1 * g.a2, g.a3, P->pitch_r, (int)P->mode, P->rsh[0][0], P->rsh[0][1], s),
                          "input shadow");
+            if (P->tcf.w4) {
+                if (fwd)
+                    CDV_CUDA(tc4_shadow1(src, g.a1 * g.a2, g.a3, P->pitch_x1, (int)P->mode, P->xsh1[0][0],
+                                         P->xsh1[0][1], s), "input shadow (shifted)");
+                else
+                    CDV_CUDA(tc4_shadow1(src, g.a1 * g.a2, g.a3, P->pitch_r1, (int)P->mode, P->rsh1[0][0],
+                                         P->rsh1[0][1], s), "input shadow (shifted)");
+            }
             TcArgs t = fwd ? P->tcf : P->tca;
             t.role = ROLE_PLAIN;
             t.out = out + (int64_t)b * (fwd ? P->ny : P->nx);
@@ -684,6 +824,9 @@ static cdv_status run_phase(void* vctx, int phase, bool loop, unsigned long long
         if (P->tc())
             CDV_CUDA(tc_shadow(R.X, P->m[0] * P->m[1], P->m[2], P->pitch_x, (int)P->mode, P->xsh[0][0], P->xsh[0][1], s),
                      "x0 shadow");
+        if (P->tc() && P->tcf.w4)
+            CDV_CUDA(tc4_shadow1(R.X, P->m[0] * P->m[1], P->m[2], P->pitch_x1, (int)P->mode, P->xsh1[0][0],
+                                 P->xsh1[0][1], s), "x0 shadow (shifted)");
         CDV_CUDA(launch_state_init(P->st, R.o.delta0, P->absum, R.o.beta, R.o.max_halvings, R.o.max_rejects, R.K,
                                    kHistCap, R.o.tikhonov, R.o.armijo, R.o.bb, s), "state");
         if (R.o.tikhonov != 0.0) CDV_CUDA(launch_sumsq(R.X, P->nx, P->part_x, s), "||x_0||^2");

@@ -206,6 +206,16 @@ struct TcArgs {
     void* sh_out_lo[2];
     int* err;            // device error word
     long long wait_cycles;   // budget of each barrier wait in the work loops (clock64 cycles)
+    // narrow form (conv_tc4.cuh): 4 output columns per tile, 32 output-plane slots
+    int w4;              // 1: this direction runs the narrow kernel
+    int pc;              // output planes per tile (a multiple of 32)
+    int kc;              // 16-byte chunks of the window of 4 + q3 - 1 columns
+    int steps;           // MMA K steps per input plane: ceil(q2 * kc / 2)
+    int spst;            // K steps per template stage (= kc: two template rows)
+    int nst;             // template stages per input plane
+    int64_t sh_pitch1;   // row pitch of the output shadows shifted by 4 columns
+    void* sh_out_hi1[2];
+    void* sh_out_lo1[2];
     IterCtx ctx;
 };
 constexpr long long kTcWaitCycles = 1000000000ll;   // default budget, about 0.5 s
@@ -216,6 +226,18 @@ cudaError_t tc_build_btiles(const float* w, int q1, int q2, int q3, int D, int K
                             void* lo, cudaStream_t s);
 cudaError_t tc_shadow(const float* src, int64_t a1a2, int64_t a3, int64_t pitch, int kind, void* hi, void* lo,
                       cudaStream_t s);
+// Narrow form (conv_tc4.cu): shared-memory bytes, launch (maps: copy 0 hi0 lo0 hi1 lo1, then copy 1),
+// template stages ([part][stage][version][group][chunk][8 rows][16 B]), the shifted shadow copy
+// (column c at c + 4 of a row of pitch1; columns 0-3 are never written and must hold zeros).
+size_t tc4_smem_bytes(const TcArgs& t);
+size_t tc4_btiles_bytes(const TcArgs& t);
+cudaError_t tc4_prepare(int kind);
+cudaError_t tc4_launch(const TcArgs& t, const struct CUtensorMap_st* maps, cudaStream_t s);
+cudaError_t tc4_build_btiles(const TcArgs& t, const float* w, void* hi, void* lo, cudaStream_t s);
+cudaError_t tc4_shadow1(const float* src, int64_t a1a2, int64_t a3, int64_t pitch1, int kind, void* hi, void* lo,
+                        cudaStream_t s);
+double tc4_executed_macs(const TcArgs& t);
+double tc4_model_cycles(const TcArgs& t);
 
 // FFT comparator (fft.cu): cuFFT plans over the zero-padded grid of N_i >= m_i + 2p_i samples.
 struct FftPlan {

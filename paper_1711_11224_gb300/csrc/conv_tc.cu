@@ -14,11 +14,14 @@ cudaError_t tc_launch_var(const TcArgs& t, const CUtensorMap* maps, cudaStream_t
 cudaError_t tc_prepare(int kind)
 {
     cudaError_t e = tc_prepare_kinds<false>(kind);
-    return e == cudaSuccess ? tc_prepare_var(kind) : e;
+    if (e == cudaSuccess) e = tc_prepare_var(kind);
+    return e == cudaSuccess ? tc4_prepare(kind) : e;
 }
 
+// maps: 4 tensor maps (copy 0: hi0 lo0 hi1 lo1), 8 for the narrow kernel (then copy 1)
 cudaError_t tc_launch(const TcArgs& t, const CUtensorMap* maps, cudaStream_t s)
 {
+    if (t.w4) return tc4_launch(t, maps, s);
     if ((t.W != 8 && t.W != 16) || t.P * t.W != kNT) return cudaErrorInvalidValue;
     if (t.var) return tc_launch_var(t, maps, s);
     return tc_launch_kinds<false>(t, maps, s);

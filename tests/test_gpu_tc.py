@@ -168,8 +168,9 @@ def test_tc_rl_is_fp32_only():
 
 
 @pytest.mark.parametrize("mode", ["split3", "bf16", "tf32"])
-def test_tc_describe_counts_the_kernel_loops(mode):
-    """Executed MACs the library reports, recounted here from the tiling it reports."""
+def test_tc_describe_counts_the_kernel_loops(mode, monkeypatch):
+    """Executed MACs the library reports for the wide kernel, recounted here from the tiling it reports."""
+    monkeypatch.setenv("CDV_TC_KERNEL", "wide")
     m, q = (40, 300, 130), (31, 31, 21)
     p = [(v - 1) // 2 for v in q]
     with _plan(m, q, mode) as pl:
