@@ -84,6 +84,12 @@ int cdv_version(void);
  * axis; p[0..n-1] >= 0 half-widths of H (H has 2p_i+1 samples per axis).
  * Allocates the workspace on the current CUDA device (the plan is bound to
  * it).  *out receives the plan, or NULL on error.
+ * Tensor-core modes pick between two kernels by a cycle model (the wide one,
+ * 8 or 16 output columns per tile; the narrow one, 4 columns and 32 sliding
+ * output-plane slots, for BF16 forms with q1 <= 31 and q3 = 1 mod 4).  The
+ * environment variable CDV_TC_KERNEL, read here, overrides the choice:
+ * "wide", "narrow", "narrow_rows" or "narrow_flat" (the narrow kernel with the
+ * forward's tiles over rows only, or over column groups and rows).
  */
 cdv_status cdv_plan_create(cdv_plan** out, int n, const int64_t* m, const int32_t* p,
                            cdv_mode mode, void* stream);

@@ -88,6 +88,7 @@ struct cdv_plan {
     void* rsh1[2][2] = {};
     int64_t pitch_x = 0, pitch_r = 0, pitch_x1 = 0, pitch_r1 = 0;
     CUtensorMap map_x[8], map_r[8]; // hi0, lo0, hi1, lo1 of copy 0, then of copy 1 (narrow kernel)
+    std::vector<int4> tc4_list[2];  // narrow kernel: host copy of the tile lists (forward, adjoint)
     int* dev_err = nullptr;
     bool tc() const { return mode == CDV_MODE_BF16 || mode == CDV_MODE_TF32 || mode == CDV_MODE_SPLIT_BF16X3; }
     bool fft() const { return mode == CDV_MODE_FFT; }
@@ -241,11 +242,11 @@ static double tc_wide_makespan(const TcArgs& t)
 // Narrow-kernel template of one direction from the wide one (shared fields), with pc output planes
 // per tile; false if the direction cannot run it (TF32, q1 > 31, windows not 4-column aligned, or
 // too little shared memory).
-static bool tc4_config(const cdv_plan* P, const TcArgs& wide, int pc, TcArgs& t)
+static bool tc4_config(const cdv_plan* P, const TcArgs& wide, bool flat, TcArgs& t)
 {
     const ConvGeom& g = wide.g;
-    if (P->mode == CDV_MODE_TF32 || g.q1 > 31 || ((g.o3 - (g.q3 - 1)) % 4 + 4) % 4 != 0 || pc % 32 != 0 || pc < 32)
-        return false;
+    const int pc = 32;                       // tile lists cut the planes into 32-aligned ranges (tc4_partition)
+    if (P->mode == CDV_MODE_TF32 || g.q1 > 31 || ((g.o3 - (g.q3 - 1)) % 4 + 4) % 4 != 0) return false;
     t = wide;
     t.w4 = 1;
     t.W = 4;
@@ -262,6 +263,34 @@ static bool tc4_config(const cdv_plan* P, const TcArgs& wide, int pc, TcArgs& t)
     t.tiles1 = ceil_div(g.b1, pc);
     t.tiles2 = ceil_div(g.b2, 128 * t.MT);
     t.tiles3 = ceil_div(g.b3, 4);
+    t.flat = 0;
+    if (flat) {
+        // the forward of a full convolution (o2 = 0, b2 = a2 + q2 - 1): rows that spill past a group's
+        // lp rows read the next group's leading rows, which are zero, so M can run across groups
+        if (g.o2 != 0 || g.b2 != g.a2 + g.q2 - 1) return false;
+        t.flat = 1;
+        t.lp = (int)((g.b2 + 31) / 32 * 32);
+        for (int c = 0; c < 2; c++) {
+            t.ngrp[c] = 0;
+            t.gfirst[c] = -1;
+        }
+        for (int gi = 0; gi < t.tiles3; gi++) {
+            const int64_t x = 4 * (int64_t)gi + g.o3 - (g.q3 - 1);
+            const int c = (((x % 8) + 8) % 8) == 0 ? 0 : 1;
+            if (t.gfirst[c] < 0) t.gfirst[c] = gi;
+            t.ngrp[c]++;
+        }
+        for (int c = 0; c < 2; c++) {
+            if (t.gfirst[c] < 0) t.gfirst[c] = 0;
+            t.nblk[c] = ceil_div((int64_t)t.ngrp[c] * t.lp, 128 * t.MT);
+        }
+        // staged rows: 256 M rows, then (kc - 1) chunks of lp rows and q2 - 1 row shifts further
+        t.fboxes = ceil_div(128 * t.MT + (int64_t)(t.kc - 1) * t.lp + g.q2 - 1, 32);
+        if (2 * t.lp + 1 >= (1 << 14) || t.fboxes * 32 + 2 * t.lp >= (1 << 14)) return false;
+        t.tiles2 = 1;
+        t.tiles3 = t.nblk[0] + t.nblk[1];
+        if ((int64_t)t.ngrp[0] * t.lp >= (1LL << 30) || (int64_t)t.ngrp[1] * t.lp >= (1LL << 30)) return false;
+    }
     const int64_t ntiles = (int64_t)t.tiles1 * t.tiles2 * t.tiles3;
     if (ntiles > (1LL << 31) - 1) return false;
     t.ntiles = (int)ntiles;
@@ -277,7 +306,7 @@ static bool tc4_config(const cdv_plan* P, const TcArgs& wide, int pc, TcArgs& t)
 }
 
 static cudaError_t make_map(CUtensorMap* m, const cdv_plan* P, void* base, int64_t d1, int64_t d2, int64_t d3,
-                            int64_t pitch)
+                            int64_t pitch, int box_rows)
 {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
@@ -285,7 +314,7 @@ static cudaError_t make_map(CUtensorMap* m, const cdv_plan* P, void* base, int64
     const int es = tf ? 4 : 2, ept = tf ? 4 : 8;
     cuuint64_t dims[3] = {(cuuint64_t)d3, (cuuint64_t)d2, (cuuint64_t)d1};
     cuuint64_t strides[2] = {(cuuint64_t)(pitch * es), (cuuint64_t)(d2 * pitch * es)};
-    cuuint32_t box[3] = {(cuuint32_t)ept, (cuuint32_t)(P->tcf.rows / 2), 1};
+    cuuint32_t box[3] = {(cuuint32_t)ept, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(m, tf ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims,
                      strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -306,21 +335,35 @@ static cudaError_t tc_setup(cdv_plan* P)
     // The narrow kernel runs both directions or neither (each direction's epilogue writes the input
     // shadows of the other); CDV_TC_KERNEL=wide|narrow overrides the cycle model.
     {
+        // narrow_rows / narrow_flat: the narrow kernel with the forward's M over rows only / over
+        // (column group, row) whenever that is possible
         const char* env = getenv("CDV_TC_KERNEL");
-        const bool force_wide = env && strcmp(env, "wide") == 0, force_narrow = env && strcmp(env, "narrow") == 0;
+        const bool force_wide = env && strcmp(env, "wide") == 0;
+        const bool no_flat = env && strcmp(env, "narrow_rows") == 0, only_flat = env && strcmp(env, "narrow_flat") == 0;
+        const bool force_narrow = env && (strcmp(env, "narrow") == 0 || no_flat || only_flat);
         TcArgs best[2];
+        std::vector<int4> blist[2];
+        std::vector<int> boff[2];
         double cost[2] = {-1.0, -1.0};
-        for (int d = 0; d < 2; d++) {
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+            nsm = 0;
+        for (int d = 0; d < 2 && nsm > 0; d++) {
             const TcArgs& wide = d ? P->tca : P->tcf;
-            for (int pc = 32; pc <= 256; pc += 32) {
+            for (int fl = 0; fl < (d == 0 ? 2 : 1); fl++) {
                 TcArgs c;
-                if (!tc4_config(P, wide, pc, c)) continue;
-                const double mk = tc4_model_cycles(c);
+                if ((fl && no_flat) || !tc4_config(P, wide, fl != 0, c)) continue;
+                if (only_flat && d == 0 && !c.flat && tc4_config(P, wide, true, c)) continue;
+                std::vector<int4> L;
+                std::vector<int> O;
+                const double mk = tc4_partition(c, nsm, L, O);
                 if (cost[d] < 0.0 || mk < cost[d]) {
                     cost[d] = mk;
                     best[d] = c;
+                    blist[d] = L;
+                    boff[d] = O;
                 }
-                if (c.tiles1 == 1) break;
             }
         }
         const bool legal = cost[0] >= 0.0 && cost[1] >= 0.0;
@@ -328,6 +371,21 @@ static cudaError_t tc_setup(cdv_plan* P)
         if (legal && !force_wide && (force_narrow || cost[0] + cost[1] < wide_cost)) {
             P->tcf = best[0];
             P->tca = best[1];
+            for (int d = 0; d < 2; d++) {
+                TcArgs& t = d ? P->tca : P->tcf;
+                int4* L = nullptr;
+                int* O = nullptr;
+                cudaError_t e2 = P->alloc(&L, blist[d].size());
+                if (e2 == cudaSuccess) e2 = P->alloc(&O, boff[d].size());
+                if (e2 == cudaSuccess)
+                    e2 = cudaMemcpy(L, blist[d].data(), blist[d].size() * sizeof(int4), cudaMemcpyHostToDevice);
+                if (e2 == cudaSuccess)
+                    e2 = cudaMemcpy(O, boff[d].data(), boff[d].size() * sizeof(int), cudaMemcpyHostToDevice);
+                if (e2 != cudaSuccess) return e2;
+                t.tlist = L;
+                t.toff = O;
+                P->tc4_list[d] = blist[d];
+            }
         }
     }
     const bool w4 = P->tcf.w4 != 0;
@@ -378,17 +436,21 @@ static cudaError_t tc_setup(cdv_plan* P)
     }
     for (int b = 0; b < 2; b++)
         for (int p = 0; p < 2; p++) {
-            if ((e = make_map(&P->map_x[2 * b + p], P, P->xsh[b][p], P->m[0], P->m[1], P->m[2], P->pitch_x)) != cudaSuccess)
+            // the forward reads X through 32-row boxes in the flat layout, else through two boxes of half the
+            // staged rows; the adjoint reads R through the latter
+            const int bx = P->tcf.flat ? 32 : P->tcf.rows / 2, br = P->tca.rows / 2;
+            if ((e = make_map(&P->map_x[2 * b + p], P, P->xsh[b][p], P->m[0], P->m[1], P->m[2], P->pitch_x, bx)) !=
+                cudaSuccess)
                 return e;
-            if ((e = make_map(&P->map_r[2 * b + p], P, P->rsh[b][p], P->gf.b1, P->gf.b2, P->gf.b3, P->pitch_r)) !=
+            if ((e = make_map(&P->map_r[2 * b + p], P, P->rsh[b][p], P->gf.b1, P->gf.b2, P->gf.b3, P->pitch_r, br)) !=
                 cudaSuccess)
                 return e;
             if (!w4) continue;
             if ((e = make_map(&P->map_x[4 + 2 * b + p], P, P->xsh1[b][p], P->m[0], P->m[1], P->m[2] + 4,
-                              P->pitch_x1)) != cudaSuccess)
+                              P->pitch_x1, bx)) != cudaSuccess)
                 return e;
             if ((e = make_map(&P->map_r[4 + 2 * b + p], P, P->rsh1[b][p], P->gf.b1, P->gf.b2, P->gf.b3 + 4,
-                              P->pitch_r1)) != cudaSuccess)
+                              P->pitch_r1, br)) != cudaSuccess)
                 return e;
         }
     for (int b = 0; b < 2; b++) {
@@ -672,7 +734,7 @@ cdv_status cdv_plan_describe(const cdv_plan* plan, cdv_plan_info* out)
             out->K[d] = t.K;
             out->grid[d] = t.grid;
             out->tiles[d] = t.ntiles;
-            out->executed_macs[d] = t.w4 ? tc4_executed_macs(t) : tc_executed_macs(t);
+            out->executed_macs[d] = t.w4 ? tc4_executed_macs(t, plan->tc4_list[d]) : tc_executed_macs(t);
         }
     }
     return CDV_OK;

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/cdv.h"
 
 namespace cdv {
@@ -214,6 +216,19 @@ struct TcArgs {
     int spst;            // K steps per template stage (= kc: two template rows)
     int nst;             // template stages per input plane
     int64_t sh_pitch1;   // row pitch of the output shadows shifted by 4 columns
+    // forward only: M runs over (column group, row) of the groups of one shadow copy, rows padded to
+    // lp (a multiple of 32, >= b2); the input tile is staged in 32-row boxes
+    int flat;
+    int lp;
+    int fboxes;          // 32-row boxes per part of one staged input plane
+    int ngrp[2];         // column groups per shadow copy
+    int gfirst[2];       // first column group of each copy
+    int nblk[2];         // 256-row M blocks per copy
+    // per-CTA tile lists: CTA b walks tlist[toff[b] .. toff[b + 1]), each tile {S1, s1_end, combo, 0}:
+    // output planes [S1, s1_end) (S1 a multiple of 32) of M block `combo` (flat: index over the copies'
+    // blocks; else row block * column groups + column group)
+    const int4* tlist;
+    const int* toff;
     void* sh_out_hi1[2];
     void* sh_out_lo1[2];
     IterCtx ctx;
@@ -236,8 +251,10 @@ cudaError_t tc4_launch(const TcArgs& t, const struct CUtensorMap_st* maps, cudaS
 cudaError_t tc4_build_btiles(const TcArgs& t, const float* w, void* hi, void* lo, cudaStream_t s);
 cudaError_t tc4_shadow1(const float* src, int64_t a1a2, int64_t a3, int64_t pitch1, int kind, void* hi, void* lo,
                         cudaStream_t s);
-double tc4_executed_macs(const TcArgs& t);
-double tc4_model_cycles(const TcArgs& t);
+// Balanced tile lists for the narrow kernel (host): fills the tile lists and the grid, returns the
+// modelled makespan in cycles; tc4_executed_macs counts the MMAs of those lists.
+double tc4_partition(TcArgs& t, int nsm, std::vector<int4>& list, std::vector<int>& off);
+double tc4_executed_macs(const TcArgs& t, const std::vector<int4>& list);
 
 // FFT comparator (fft.cu): cuFFT plans over the zero-padded grid of N_i >= m_i + 2p_i samples.
 struct FftPlan {

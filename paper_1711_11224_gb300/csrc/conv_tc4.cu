@@ -21,7 +21,8 @@ cudaError_t tc4_prepare(int kind)
 
 cudaError_t tc4_launch(const TcArgs& t, const CUtensorMap* maps, cudaStream_t s)
 {
-    if (!t.w4 || t.kc < 1 || t.spst != t.kc || t.nst * t.spst < t.steps) return cudaErrorInvalidValue;
+    if (!t.w4 || t.kc < 1 || t.spst != t.kc || t.nst * t.spst < t.steps || !t.tlist || !t.toff)
+        return cudaErrorInvalidValue;
     if (t.var) return tc4_launch_var(t, maps, s);
     return tc4_launch_kinds<false>(t, maps, s);
 }
@@ -100,42 +101,104 @@ cudaError_t tc4_shadow1(const float* src, int64_t a1a2, int64_t a3, int64_t pitc
 
 namespace cdv {
 
+// Modelled tensor-pipe cycles of the MMAs of one tile: each MMA costs about max(46, N / 2) cycles.
+static double tc4_tile_cycles(const TcArgs& t, const Tc4Tile& C)
+{
+    double c = 0.0;
+    for (int64_t u = C.ulo; u <= C.uhi; u++) {
+        int k0, ns;
+        C.mma_slots(t.g, u, k0, ns);
+        c += std::max(46.0, kW4 * ns / 2.0);
+    }
+    return c * t.steps * (double)C.mtiles(t);
+}
+
 // Tensor-pipe work of one launch of the narrow kernel, counting its loops: per tile and input plane,
 // `steps` MMAs of K = 16 and N = 4 x (slots covered) for each 128-row M tile holding outputs.
-double tc4_executed_macs(const TcArgs& t)
+double tc4_executed_macs(const TcArgs& t, const std::vector<int4>& list)
 {
-    const ConvGeom& g = t.g;
     double macs = 0.0;
-    for (int tile = 0; tile < t.ntiles; tile++) {
-        const Tc4Tile C = Tc4Tile::make(t, tile);
-        const int64_t nmt = std::min<int64_t>(kMT, (g.b2 - C.S2 + kM - 1) / kM);
+    for (const int4& d : list) {
+        const Tc4Tile C = Tc4Tile::make(t, d);
         for (int64_t u = C.ulo; u <= C.uhi; u++) {
             int k0, ns;
-            C.mma_slots(g, u, k0, ns);
-            macs += (double)t.steps * 16.0 * (double)(kW4 * ns) * (double)(kM * nmt);
+            C.mma_slots(t.g, u, k0, ns);
+            macs += (double)t.steps * 16.0 * (double)(kW4 * ns) * (double)(kM * C.mtiles(t));
         }
     }
     return macs * ((t.nprec == 2) ? 3.0 : 1.0);
 }
 
-// Modelled tensor-pipe cycles of one launch: each MMA costs about max(46, N / 2) cycles, and the
-// persistent CTAs take tiles blockIdx.x, blockIdx.x + grid, ... (the slowest CTA sets the time).
-double tc4_model_cycles(const TcArgs& t)
+// Tile lists of the persistent CTAs.  The output is a sequence of M blocks (combos), each with all b1
+// output planes; it is cut into tiles of 32-aligned plane ranges and dealt out in order: every CTA
+// takes the longest plane ranges that keep its modelled load under a bound T, and T is the smallest
+// bound (binary search) for which nsm CTAs suffice.  Long ranges waste less at the plane-chunk ends
+// (where an input plane reaches few slots); the bound balances the CTAs.
+double tc4_partition(TcArgs& t, int nsm, std::vector<int4>& list, std::vector<int>& off)
 {
     const ConvGeom& g = t.g;
-    std::vector<double> cta(std::max(1, t.grid), 0.0);
-    for (int tile = 0; tile < t.ntiles; tile++) {
-        const Tc4Tile C = Tc4Tile::make(t, tile);
-        const int64_t nmt = std::min<int64_t>(kMT, (g.b2 - C.S2 + kM - 1) / kM);
-        double c = 0.0;
-        for (int64_t u = C.ulo; u <= C.uhi; u++) {
-            int k0, ns;
-            C.mma_slots(g, u, k0, ns);
-            c += std::max(46.0, kW4 * ns / 2.0);
+    const int ncombo = t.flat ? t.nblk[0] + t.nblk[1] : t.tiles2 * t.tiles3;
+    const int nb = (int)((g.b1 + 31) / 32);                  // 32-plane units
+    // cycles of planes [32a, min(32e, b1)) of a combo with one M tile (a < e), cached
+    std::vector<double> cost((size_t)nb * (nb + 1), -1.0);
+    auto chunk = [&](int a, int e) {
+        double& c = cost[(size_t)a * (nb + 1) + e];
+        if (c < 0.0) {
+            TcArgs one = t;
+            one.flat = 0;
+            one.tiles2 = 1;
+            one.tiles3 = 1;
+            const Tc4Tile C = Tc4Tile::make(one, make_int4(32 * a, (int)std::min<int64_t>(32 * (int64_t)e, g.b1), 0, 0));
+            // one M tile of outputs (S2 = 0 with b2 of at least one row): scaled by the combo's M tiles below
+            c = tc4_tile_cycles(one, C) / std::max(1, C.mtiles(one));
         }
-        cta[tile % cta.size()] += c * t.steps * (double)nmt;
+        return c;
+    };
+    std::vector<int> nmt(ncombo);
+    for (int j = 0; j < ncombo; j++) nmt[j] = Tc4Tile::make(t, make_int4(0, (int)g.b1, j, 0)).mtiles(t);
+    auto deal = [&](double T, std::vector<int4>* L, std::vector<int>* O) -> int {
+        int cta = 0;
+        double load = 0.0;
+        if (O) O->assign(1, 0);
+        for (int j = 0; j < ncombo; j++) {
+            int a = 0;
+            while (a < nb) {
+                int e = a;
+                while (e < nb && load + chunk(a, e + 1) * nmt[j] <= T) e++;
+                if (e == a) {
+                    if (load == 0.0) return 1 << 30;             // one 32-plane tile exceeds T
+                    if (O) O->push_back((int)L->size());
+                    cta++;
+                    load = 0.0;
+                    continue;
+                }
+                if (L) L->push_back(make_int4(32 * a, (int)std::min<int64_t>(32 * (int64_t)e, g.b1), j, 0));
+                load += chunk(a, e) * nmt[j];
+                a = e;
+            }
+        }
+        if (O) O->push_back((int)L->size());
+        return cta + 1;
+    };
+    double hi = 0.0;
+    for (int j = 0; j < ncombo; j++) hi += chunk(0, nb) * nmt[j];
+    double lo = 0.0;
+    for (int it = 0; it < 60 && hi - lo > 1e-4 * hi; it++) {
+        const double mid = 0.5 * (lo + hi);
+        if (deal(mid, nullptr, nullptr) <= nsm) hi = mid;
+        else lo = mid;
     }
-    return *std::max_element(cta.begin(), cta.end());
+    list.clear();
+    deal(hi, &list, &off);
+    t.grid = (int)off.size() - 1;
+    t.ntiles = (int)list.size();
+    double mk = 0.0;
+    for (int b = 0; b < t.grid; b++) {
+        double c = 0.0;
+        for (int k = off[b]; k < off[b + 1]; k++) c += tc4_tile_cycles(t, Tc4Tile::make(t, list[k]));
+        mk = std::max(mk, c);
+    }
+    return mk;
 }
 
 }  // namespace cdv

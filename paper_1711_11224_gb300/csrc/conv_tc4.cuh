@@ -70,7 +70,7 @@ struct Tc4Smem {
     __host__ __device__ static Tc4Smem make(const TcArgs& t)
     {
         Tc4Smem s;
-        s.a_bytes = (size_t)t.kc * t.rows * 16;                         // one part of one input plane
+        s.a_bytes = t.flat ? (size_t)t.fboxes * 32 * 16 : (size_t)t.kc * t.rows * 16;   // one part of one input plane
         s.b_bytes = (size_t)(kSlots / 2) * (2 * t.spst) * 128;           // one part of one stage
         s.off_b = (size_t)t.na * t.nprec * s.a_bytes;
         s.off_bar = s.off_b + (size_t)t.ns * t.nprec * s.b_bytes;
@@ -84,28 +84,48 @@ struct Tc4Smem {
 // One tile of the narrow kernel: output planes [S1, s1_end) (S1 a multiple of 32), rows
 // [S2, S2 + 256), columns [S3, S3 + 4), input planes [ulo, uhi]; par = the shadow copy in which the
 // window of the tile starts on a chunk.
+// Flat tiles (forward): M row f of block f0 is row f mod lp of column group gfirst + 2 (f / lp) of the
+// tile's shadow copy; rows f >= nf (or rows >= b2) hold no outputs.
 struct Tc4Tile {
     int64_t S1, S2, S3, s1_end, ulo, uhi;
     int par;
-    __host__ __device__ static Tc4Tile make(const TcArgs& T, int tile)
+    int64_t f0, nf;      // flat tiles: first M row, M rows holding groups
+    int x0;              // TMA column of window chunk 0 (of the first group of the copy, for flat tiles)
+    __host__ __device__ static Tc4Tile make(const TcArgs& T, int4 d)
     {
         Tc4Tile c;
-        const int t3 = tile % T.tiles3;
-        tile /= T.tiles3;
-        const int t2 = tile % T.tiles2;
-        const int t1 = tile / T.tiles2;
+        const int t3 = d.z % T.tiles3;
+        const int t2 = d.z / T.tiles3;
         const ConvGeom& G = T.g;
-        c.S1 = (int64_t)t1 * T.pc;
-        c.S2 = (int64_t)t2 * kM * kMT;
-        c.S3 = (int64_t)t3 * kW4;
-        c.s1_end = c.S1 + T.pc < G.b1 ? c.S1 + T.pc : G.b1;
+        c.S1 = d.x;
+        c.s1_end = d.y;
         const int64_t lo = c.S1 + G.o1 - G.q1 + 1;
         c.ulo = lo > 0 ? lo : 0;
         const int64_t hi = c.s1_end - 1 + G.o1;
         c.uhi = hi < G.a1 - 1 ? hi : G.a1 - 1;
-        const int64_t x = c.S3 + G.o3 - (G.q3 - 1);
-        c.par = (int)(((x % 8) + 8) % 8) == 0 ? 0 : 1;
+        if (T.flat) {
+            c.par = t3 < T.nblk[0] ? 0 : 1;
+            c.f0 = (int64_t)(t3 - (c.par ? T.nblk[0] : 0)) * kM * kMT;
+            c.nf = (int64_t)T.ngrp[c.par] * T.lp;
+            c.S2 = 0;
+            c.S3 = (int64_t)T.gfirst[c.par] * kW4;
+        } else {
+            c.S2 = (int64_t)t2 * kM * kMT;
+            c.S3 = (int64_t)t3 * kW4;
+            const int64_t x = c.S3 + G.o3 - (G.q3 - 1);
+            c.par = (int)(((x % 8) + 8) % 8) == 0 ? 0 : 1;
+            c.f0 = 0;
+            c.nf = 0;
+        }
+        c.x0 = (int)(c.S3 + G.o3 - (G.q3 - 1)) + (c.par ? 4 : 0);
         return c;
+    }
+    // M tiles (of 128 rows) of the tile that hold outputs
+    __host__ __device__ int mtiles(const TcArgs& T) const
+    {
+        const int64_t left = T.flat ? nf - f0 : T.g.b2 - S2;
+        const int64_t n = (left + kM - 1) / kM;
+        return (int)(n < kMT ? n : kMT);
     }
     // output planes that input plane u reaches inside the tile: [slo, shi] (empty if slo > shi)
     __host__ __device__ void planes(const ConvGeom& G, int64_t u, int64_t& slo, int64_t& shi) const
@@ -194,7 +214,7 @@ conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtens
     unsigned* tslot = reinterpret_cast<unsigned*>(sm + lay.off_bar + 384);
     volatile int* sflag = reinterpret_cast<volatile int*>(sm + lay.off_bar + 392);
 
-    const int ntiles = T.ntiles;
+    const int kt0 = T.toff[blockIdx.x], kt1 = T.toff[blockIdx.x + 1];   // this CTA's tiles
     const bool run = do_conv && *(volatile int*)T.err == 0;
 
     if (tid == 0) {
@@ -228,9 +248,11 @@ conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtens
         int bs = 0, it = 0, nb = 0;
         unsigned bph = 0;
         int a_uses[2] = {0, 0};
-        for (int tile = blockIdx.x; tile < ntiles && !*sflag; tile += gridDim.x) {
-            const Tc4Tile C = Tc4Tile::make(T, tile);
-            const int x0 = (int)(C.S3 + G.o3 - (G.q3 - 1)) + (C.par ? 4 : 0);   // a multiple of 8
+        for (int kt = kt0; kt < kt1 && !*sflag; ++kt) {
+            const Tc4Tile C = Tc4Tile::make(T, T.tlist[kt]);
+            const int x0 = C.x0;                                       // a multiple of 8
+            const int fch0 = T.flat ? (int)(C.f0 / T.lp) : 0;          // flat: chunk and row of M row f0
+            const int fr0 = T.flat ? (int)(C.f0 - (int64_t)fch0 * T.lp) : 0;
             const int64_t v0 = C.S2 + G.o2 - (G.q2 - 1);
             const CUtensorMap* mh = C.par ? (sel ? &s10 : &s00) : (sel ? &m10 : &m00);
             const CUtensorMap* ml = C.par ? (sel ? &s11 : &s01) : (sel ? &m11 : &m01);
@@ -242,10 +264,25 @@ conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtens
                 for (int p = 0; p < NPREC; p++) {
                     const CUtensorMap* mp = p ? ml : mh;
                     const unsigned dst = su32(sA + ((size_t)ab * NPREC + p) * lay.a_bytes);
-                    for (int c = 0; c < T.kc; c++)
-                        for (int h = 0; h < 2; h++)
-                            tma3(dst + (unsigned)((c * T.rows + h * half) * 16), mp, x0 + c * EPT, (int)(v0 + h * half),
-                                 (int)u, A_FULL(ab));
+                    if (T.flat) {
+                        // linear rows f0 .. f0 + 32 fboxes of the flat layout: row P is row P mod lp of
+                        // chunk P / lp (32-row boxes never cross a chunk, lp being a multiple of 32)
+                        int ch = fch0, R = fr0;
+                        for (int k = 0; k < T.fboxes; k++) {
+                            tma3(dst + (unsigned)(k * 32 * 16), mp, x0 + ch * EPT, R + G.o2 - (G.q2 - 1), (int)u,
+                                 A_FULL(ab));
+                            R += 32;
+                            if (R == T.lp) {
+                                R = 0;
+                                ++ch;
+                            }
+                        }
+                    } else {
+                        for (int c = 0; c < T.kc; c++)
+                            for (int h = 0; h < 2; h++)
+                                tma3(dst + (unsigned)((c * T.rows + h * half) * 16), mp, x0 + c * EPT,
+                                     (int)(v0 + h * half), (int)u, A_FULL(ab));
+                    }
                 }
                 int k0, nsl;
                 C.mma_slots(G, u, k0, nsl);
@@ -284,7 +321,7 @@ conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtens
         // for every input plane and tile
         uint64_t* tab = reinterpret_cast<uint64_t*>(sm + lay.off_tab);
         for (int i = lane; i < T.steps; i += 32) {
-            const StepA sa = tc4_step(i, G.q2, T.kc, T.rows);
+            const StepA sa = tc4_step(i, G.q2, T.kc, T.flat ? T.lp : T.rows);
             tab[i] = ((uint64_t)sa.lbo << 16) + (uint64_t)sa.start;
         }
         __syncwarp();
@@ -292,9 +329,9 @@ conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtens
         int bs = 0, it = 0;
         unsigned bph = 0;
         bool ok = true;
-        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-            const Tc4Tile C = Tc4Tile::make(T, tile);
-            const int nmt = (int)min((int64_t)kMT, (G.b2 - C.S2 + kM - 1) / kM);
+        for (int kt = kt0; kt < kt1 && ok; ++kt) {
+            const Tc4Tile C = Tc4Tile::make(T, T.tlist[kt]);
+            const int nmt = C.mtiles(T);
             for (int64_t u = C.ulo; u <= C.uhi; ++u, ++it) {
                 const int b = it & 1;
                 const int ab = it % T.na;
@@ -352,27 +389,52 @@ conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtens
         // fused epilogue of one complete output plane s1 of the tile: this thread's 4 values of row
         // (its lane) go through the warp's staging tile, so that each store instruction covers 8 rows x
         // 4 consecutive columns
-        auto finish = [&](const Tc4Tile& C, int64_t s1, const float* v) {
+        // Element k (of 4) of this lane in a stored plane: row k * 8 + lane / 4 of the warp's 32, column
+        // lane % 4 of the tile (the staging tile's transposed order); -1 if it holds no output.
+        auto locate = [&](const Tc4Tile& C, int64_t s1, int k, int64_t& idx, int64_t& i0, int64_t& i1) -> bool {
+            const int rr = k * 8 + (lane >> 2), c = lane & 3;
+            int64_t s2 = C.S2 + mt * kM + quarter * 32 + rr;
+            int64_t s3 = C.S3 + c;
+            if (T.flat) {
+                const int f = (int)C.f0 + mt * kM + quarter * 32 + rr;
+                if (f >= (int)C.nf) return false;
+                const int gg = f / T.lp;
+                s2 = f - gg * T.lp;
+                s3 += 8 * gg;                                         // groups of one copy are 8 columns apart
+            }
+            if (s2 >= G.b2 || s3 >= G.b3) return false;
+            const int64_t row = s1 * G.b2 + s2;
+            idx = row * G.b3 + s3;
+            i0 = row * T.sh_pitch + s3;
+            i1 = row * T.sh_pitch1 + s3 + 4;
+            return true;
+        };
+        // the input the fused epilogue reads for an element (y for the residual, x_k for the update)
+        auto operand = [&](int64_t idx) -> float {
+            if (role == ROLE_FWD_INIT || role == ROLE_FWD_TRIAL) return T.ctx.y[idx];
+            if (role == ROLE_ADJ_TRIAL) return xin[idx];
+            return 0.f;
+        };
+        // fused epilogue of one complete output plane s1 of the tile: this thread's 4 values of row
+        // (its lane) go through the warp's staging tile, so that each store instruction covers 8 rows x
+        // 4 consecutive columns; pre[] holds the operands if they were loaded ahead
+        auto finish = [&](const Tc4Tile& C, int64_t s1, const float* v, const float* pre) {
             __syncwarp();
             reinterpret_cast<float4*>(stg)[lane] = make_float4(v[0], v[1], v[2], v[3]);
             __syncwarp();
 #pragma unroll
             for (int k = 0; k < 4; k++) {
-                const int rr = k * 8 + (lane >> 2), c = lane & 3;
-                const float val = stg[rr * 4 + c];
-                const int64_t s2 = C.S2 + mt * kM + quarter * 32 + rr;
-                const int64_t s3 = C.S3 + c;
-                if (s2 >= G.b2 || s3 >= G.b3) continue;
-                const int64_t row = s1 * G.b2 + s2;
-                const int64_t idx = row * G.b3 + s3;
-                const int64_t i0 = row * T.sh_pitch + s3, i1 = row * T.sh_pitch1 + s3 + 4;
+                const float val = stg[(k * 8 + (lane >> 2)) * 4 + (lane & 3)];
+                int64_t idx, i0, i1;
+                if (!locate(C, s1, k, idx, i0, i1)) continue;
+                const float opd = pre ? pre[k] : operand(idx);
                 switch (role) {
                 case ROLE_PLAIN:
                     out[idx] = val;
                     break;
                 case ROLE_FWD_INIT:
                 case ROLE_FWD_TRIAL: {
-                    const float rr2 = val - T.ctx.y[idx];
+                    const float rr2 = val - opd;
                     out[idx] = rr2;
                     store_shadow<KIND>(T.sh_out_hi[sel], T.sh_out_lo[sel], i0, rr2);
                     store_shadow<KIND>(T.sh_out_hi1[sel], T.sh_out_lo1[sel], i1, rr2);
@@ -381,7 +443,7 @@ conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtens
                 }
                 case ROLE_ADJ_TRIAL: {
                     float gg;
-                    const float xo = xin[idx];
+                    const float xo = opd;
                     if (do_conv) {
                         gg = val;
                         if (VAR && want_sy) {
@@ -410,9 +472,9 @@ conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtens
                 }
             }
         };
-        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-            const Tc4Tile C = Tc4Tile::make(T, tile);
-            const bool rows_in = C.S2 + mt * kM < G.b2;
+        for (int kt = kt0; kt < kt1 && ok; ++kt) {
+            const Tc4Tile C = Tc4Tile::make(T, T.tlist[kt]);
+            const bool rows_in = mt < C.mtiles(T);
             float tot[kSlots][kW4];
 #pragma unroll
             for (int i = 0; i < kSlots; i++)
@@ -421,11 +483,23 @@ conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtens
             if (!run) {
                 // a retried trial reuses the stored gradient: only the update, for every plane of the tile
                 if (!do_conv && rows_in && *(volatile int*)T.err == 0)
-                    for (int64_t s1 = C.S1; s1 < C.s1_end; ++s1) finish(C, s1, &tot[0][0]);
+                    for (int64_t s1 = C.S1; s1 < C.s1_end; ++s1) finish(C, s1, &tot[0][0], nullptr);
                 continue;
             }
             for (int64_t u = C.ulo; u <= C.uhi; ++u, ++it) {
                 const int b = it & 1;
+                // the plane completed by u (before the last input plane: only u - o1) and its operands,
+                // loaded while the MMAs of u run
+                const int64_t sdone = u - G.o1;
+                const bool one = rows_in && u < G.a1 - 1 && sdone >= C.S1 && sdone < C.s1_end;
+                float pre[4] = {0.f, 0.f, 0.f, 0.f};
+                if (one) {
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        int64_t idx, i0, i1;
+                        if (locate(C, sdone, k, idx, i0, i1)) pre[k] = operand(idx);
+                    }
+                }
                 bool w = mbar_wait(ACC_FULL(b), (unsigned)((it >> 1) & 1), T.wait_cycles);
                 w = __all_sync(0xffffffffu, w && !*sflag);
                 if (!w) {
@@ -440,18 +514,18 @@ conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtens
                     const int klo = (int)(slo % kSlots);
                     const int span = (int)(shi - slo);
 #pragma unroll
-                    for (int pr = 0; pr < kSlots / 2; pr++) {
-                        const int ka = 2 * pr, kb = 2 * pr + 1;
-                        const bool va = ((ka - klo + kSlots) % kSlots) <= span;
-                        const bool vb = ((kb - klo + kSlots) % kSlots) <= span;
-                        if (!va && !vb) continue;                         // warp-uniform
-                        float v[8];
-                        tmem_ld<8>(tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)((mt * 2 + b) * kNT + ka * kW4), v);
+                    for (int qd = 0; qd < kSlots / 4; qd++) {             // 4 slots (16 columns) per load
+                        bool vk[4];
 #pragma unroll
-                        for (int c = 0; c < kW4; c++) {
-                            if (va) tot[ka][c] += v[c];
-                            if (vb) tot[kb][c] += v[kW4 + c];
-                        }
+                        for (int e = 0; e < 4; e++) vk[e] = ((4 * qd + e - klo + kSlots) % kSlots) <= span;
+                        if (!vk[0] && !vk[1] && !vk[2] && !vk[3]) continue;    // warp-uniform
+                        float v[16];
+                        tmem_ld<16>(tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)((mt * 2 + b) * kNT + 4 * qd * kW4), v);
+#pragma unroll
+                        for (int e = 0; e < 4; e++)
+#pragma unroll
+                            for (int c = 0; c < kW4; c++)
+                                if (vk[e]) tot[4 * qd + e][c] += v[kW4 * e + c];
                     }
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -477,7 +551,7 @@ conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtens
                                 tot[k][c] = 0.f;
                             }
                         }
-                    finish(C, s1, v);
+                    finish(C, s1, v, one ? pre : nullptr);
                 }
             }
         }
