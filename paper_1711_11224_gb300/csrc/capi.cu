@@ -562,12 +562,12 @@ cdv_status cdv_plan_create(cdv_plan** out, int n, const int64_t* m, const int32_
     P->tf = conv_fp32_tile(P->gf);
     P->ta = conv_fp32_tile(P->ga);
     P->nparts = std::max(std::max(P->tf.grid, P->ta.grid), std::max(fft_epilogue_blocks(), sep_blocks()));
-    P->gp = GradPsfPlan{P->m[0], P->m[1], P->m[2], P->q[0], P->q[1], P->q[2], 1,
-                        std::max(1, (152 * 4 + P->q[0] - 1) / P->q[0])};
+    P->gp = GradPsfPlan{P->m[0], P->m[1], P->m[2], P->q[0], P->q[1], P->q[2], 1, 1};
 
     cudaError_t e = cudaGetDevice(&P->device);
     if (e == cudaSuccess && conv_fp32_supported(P->q[2])) e = conv_fp32_prepare(P->q[2]);
     if (e == cudaSuccess) e = grad_psf_prepare();
+    if (e == cudaSuccess) P->gp.chunks = grad_psf_chunks(P->gp);
     if (e == cudaSuccess && small_supported(P->m, P->p)) {
         SmallRun r{};
         for (int i = 0; i < 3; i++) {

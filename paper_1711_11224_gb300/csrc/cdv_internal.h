@@ -159,6 +159,7 @@ struct GradPsfPlan {
 // launches above kGradPsfMaxSmem fail with cudaErrorInvalidConfiguration.
 constexpr size_t kGradPsfMaxSmem = 227 * 1024;
 size_t grad_psf_smem_bytes(const GradPsfPlan& g);
+int grad_psf_chunks(const GradPsfPlan& g);      // chunks for a plan (after grad_psf_prepare)
 size_t grad_psf_partials(const GradPsfPlan& g);
 cudaError_t launch_grad_psf(const GradPsfPlan& g, const float* X, const float* dY, double* partial,
                             float* dH, cudaStream_t s);
