@@ -10,7 +10,10 @@ it was computed from, which the reader checks before use.
 
 Output: OUT_DIR/ring3d_x100.npz with X (the iterate after 100 accepted steps
 of Steps 1-3 from the centre crop of Y, float32-rounded: 6e-8 relative at most),
-f (the objective history), accepted, rejected, status, input_sha256.
+f (the objective history), accepted, rejected, status, and the inputs Y and H
+with their SHA-256 (input_sha256).  The inputs travel with the result because
+the generator's library FFT blur and Poisson draws may differ in the last bits
+between machines; a reader on another machine runs on the stored inputs.
 """
 from __future__ import annotations
 
@@ -45,7 +48,7 @@ def ring3d(out_dir, K=100):
     path = os.path.join(out_dir, "ring3d_x%d.npz" % K)
     np.savez(path, X=ref["X"].astype(np.float32), f=ref["f"], accepted=ref["accepted"],
              rejected=ref["rejected"], status=ref["status"], input_sha256=input_sha256(P),
-             seconds=dt, threads=oracle.num_threads())
+             seconds=dt, threads=oracle.num_threads(), Y=P.Y, H=P.H, K=P.K)
     return path, dt
 
 

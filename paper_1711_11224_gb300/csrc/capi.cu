@@ -355,14 +355,23 @@ static cudaError_t tc_setup(cdv_plan* P)
                 TcArgs c;
                 if ((fl && no_flat) || !tc4_config(P, wide, fl != 0, c)) continue;
                 if (only_flat && d == 0 && !c.flat && tc4_config(P, wide, true, c)) continue;
-                std::vector<int4> L;
-                std::vector<int> O;
-                const double mk = tc4_partition(c, nsm, L, O);
-                if (cost[d] < 0.0 || mk < cost[d]) {
-                    cost[d] = mk;
-                    best[d] = c;
-                    blist[d] = L;
-                    boff[d] = O;
+                // the free cut (pc = 0) or chunk-major lists of pc planes (CDV_TC_DEAL=free|chunks
+                // restricts the choice)
+                const char* deal = getenv("CDV_TC_DEAL");
+                for (int pc = 0; pc <= 512; pc += 32) {
+                    if (deal && strcmp(deal, "free") == 0 && pc > 0) break;
+                    if (deal && strcmp(deal, "chunks") == 0 && pc == 0) continue;
+                    TcArgs cc = c;
+                    std::vector<int4> L;
+                    std::vector<int> O;
+                    const double mk = tc4_partition(cc, nsm, pc, L, O);
+                    if (cost[d] < 0.0 || mk < cost[d]) {
+                        cost[d] = mk;
+                        best[d] = cc;
+                        blist[d] = L;
+                        boff[d] = O;
+                    }
+                    if (pc >= wide.g.b1) break;
                 }
             }
         }

@@ -254,7 +254,7 @@ cudaError_t tc4_shadow1(const float* src, int64_t a1a2, int64_t a3, int64_t pitc
                         cudaStream_t s);
 // Balanced tile lists for the narrow kernel (host): fills the tile lists and the grid, returns the
 // modelled makespan in cycles; tc4_executed_macs counts the MMAs of those lists.
-double tc4_partition(TcArgs& t, int nsm, std::vector<int4>& list, std::vector<int>& off);
+double tc4_partition(TcArgs& t, int nsm, int pc, std::vector<int4>& list, std::vector<int>& off);
 double tc4_executed_macs(const TcArgs& t, const std::vector<int4>& list);
 
 // FFT comparator (fft.cu): cuFFT plans over the zero-padded grid of N_i >= m_i + 2p_i samples.

@@ -129,12 +129,14 @@ double tc4_executed_macs(const TcArgs& t, const std::vector<int4>& list)
     return macs * ((t.nprec == 2) ? 3.0 : 1.0);
 }
 
-// Tile lists of the persistent CTAs.  The output is a sequence of M blocks (combos), each with all b1
-// output planes; it is cut into tiles of 32-aligned plane ranges and dealt out in order: every CTA
-// takes the longest plane ranges that keep its modelled load under a bound T, and T is the smallest
-// bound (binary search) for which nsm CTAs suffice.  Long ranges waste less at the plane-chunk ends
-// (where an input plane reaches few slots); the bound balances the CTAs.
-double tc4_partition(TcArgs& t, int nsm, std::vector<int4>& list, std::vector<int>& off)
+// Tile lists of the persistent CTAs, dealt out in order under a load bound T (the smallest, by binary
+// search on the cycle model, for which nsm CTAs suffice):
+//  * pc = 0: M block (combo) by M block, each block's b1 output planes cut into 32-aligned ranges as
+//    long as the CTA's bound allows (long ranges waste less at the plane-chunk ends, where an input
+//    plane reaches few slots);
+//  * pc > 0: chunks of pc planes, all M blocks of a chunk before the next chunk, so that the CTAs
+//    running at the same time read the same input planes (shared through L2).
+double tc4_partition(TcArgs& t, int nsm, int pc, std::vector<int4>& list, std::vector<int>& off)
 {
     const ConvGeom& g = t.g;
     const int ncombo = t.flat ? t.nblk[0] + t.nblk[1] : t.tiles2 * t.tiles3;
@@ -160,6 +162,24 @@ double tc4_partition(TcArgs& t, int nsm, std::vector<int4>& list, std::vector<in
         int cta = 0;
         double load = 0.0;
         if (O) O->assign(1, 0);
+        if (pc > 0) {
+            const int pu = pc / 32;
+            for (int a = 0; a < nb; a += pu)
+                for (int j = 0; j < ncombo; j++) {
+                    const int e = std::min(nb, a + pu);
+                    const double c = chunk(a, e) * nmt[j];
+                    if (load > 0.0 && load + c > T) {
+                        if (O) O->push_back((int)L->size());
+                        cta++;
+                        load = 0.0;
+                    }
+                    if (c > T) return 1 << 30;
+                    if (L) L->push_back(make_int4(32 * a, (int)std::min<int64_t>(32 * (int64_t)e, g.b1), j, 0));
+                    load += c;
+                }
+            if (O) O->push_back((int)L->size());
+            return cta + 1;
+        }
         for (int j = 0; j < ncombo; j++) {
             int a = 0;
             while (a < nb) {
