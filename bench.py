@@ -828,7 +828,10 @@ def run_cdv(args):
         # the fused epilogue
         launches = 1 + 1 + 3 + 1 + slots * (3 + 3 + 1) + 1
     else:
-        launches = 1 + (0 if args.mode == "fp32" else 1) + 1 + 1 + 1 + 3 * slots + 1
+        # x0, its input shadow(s) (the narrow tensor-core kernel reads two copies), state, initial forward,
+        # initial decision, 3 per trial slot, finalize
+        shadows = 0 if args.mode == "fp32" else (2 if pl.describe()["cols"][0] == 4 else 1)
+        launches = 1 + shadows + 1 + 1 + 1 + 3 * slots + 1
 
     dtype = {"fp32": "f32", "split3": "bf16x3 (split FP32, FP32 accumulate)", "tf32": "tf32 (FP32 accumulate)",
              "fft": "f32 (cuFFT comparator)",
