@@ -284,9 +284,10 @@ static bool tc4_config(const cdv_plan* P, const TcArgs& wide, bool flat, TcArgs&
             if (t.gfirst[c] < 0) t.gfirst[c] = 0;
             t.nblk[c] = ceil_div((int64_t)t.ngrp[c] * t.lp, 128 * t.MT);
         }
-        // staged rows: 256 M rows, then (kc - 1) chunks of lp rows and q2 - 1 row shifts further
-        t.fboxes = ceil_div(128 * t.MT + (int64_t)(t.kc - 1) * t.lp + g.q2 - 1, 32);
-        if (2 * t.lp + 1 >= (1 << 14) || t.fboxes * 32 + 2 * t.lp >= (1 << 14)) return false;
+        // staged rows: per window chunk c, the 256 M rows shifted by c groups (c lp rows) plus q2 - 1
+        // row shifts, in 32-row boxes; the rows between the chunks' windows are not loaded
+        t.fboxes = ceil_div(128 * t.MT + g.q2 - 1, 32);
+        if ((int64_t)t.kc * t.fboxes * 32 + g.q2 >= (1 << 14)) return false;     // descriptor offsets
         t.tiles2 = 1;
         t.tiles3 = t.nblk[0] + t.nblk[1];
         if ((int64_t)t.ngrp[0] * t.lp >= (1LL << 30) || (int64_t)t.ngrp[1] * t.lp >= (1LL << 30)) return false;

@@ -221,7 +221,7 @@ struct TcArgs {
     // lp (a multiple of 32, >= b2); the input tile is staged in 32-row boxes
     int flat;
     int lp;
-    int fboxes;          // 32-row boxes per part of one staged input plane
+    int fboxes;          // 32-row boxes per window chunk of one staged input plane (one part)
     int ngrp[2];         // column groups per shadow copy
     int gfirst[2];       // first column group of each copy
     int nblk[2];         // 256-row M blocks per copy

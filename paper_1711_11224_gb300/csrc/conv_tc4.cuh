@@ -70,7 +70,7 @@ struct Tc4Smem {
     __host__ __device__ static Tc4Smem make(const TcArgs& t)
     {
         Tc4Smem s;
-        s.a_bytes = t.flat ? (size_t)t.fboxes * 32 * 16 : (size_t)t.kc * t.rows * 16;   // one part of one input plane
+        s.a_bytes = (size_t)t.kc * (t.flat ? t.fboxes * 32 : t.rows) * 16;   // one part of one input plane
         s.b_bytes = (size_t)(kSlots / 2) * (2 * t.spst) * 128;           // one part of one stage
         s.off_b = (size_t)t.na * t.nprec * s.a_bytes;
         s.off_bar = s.off_b + (size_t)t.ns * t.nprec * s.b_bytes;
@@ -251,7 +251,7 @@ conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtens
         for (int kt = kt0; kt < kt1 && !*sflag; ++kt) {
             const Tc4Tile C = Tc4Tile::make(T, T.tlist[kt]);
             const int x0 = C.x0;                                       // a multiple of 8
-            const int fch0 = T.flat ? (int)(C.f0 / T.lp) : 0;          // flat: chunk and row of M row f0
+            const int fch0 = T.flat ? (int)(C.f0 / T.lp) : 0;          // flat: group and row of M row f0
             const int fr0 = T.flat ? (int)(C.f0 - (int64_t)fch0 * T.lp) : 0;
             const int64_t v0 = C.S2 + G.o2 - (G.q2 - 1);
             const CUtensorMap* mh = C.par ? (sel ? &s10 : &s00) : (sel ? &m10 : &m00);
@@ -265,16 +265,20 @@ conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtens
                     const CUtensorMap* mp = p ? ml : mh;
                     const unsigned dst = su32(sA + ((size_t)ab * NPREC + p) * lay.a_bytes);
                     if (T.flat) {
-                        // linear rows f0 .. f0 + 32 fboxes of the flat layout: row P is row P mod lp of
-                        // chunk P / lp (32-row boxes never cross a chunk, lp being a multiple of 32)
-                        int ch = fch0, R = fr0;
-                        for (int k = 0; k < T.fboxes; k++) {
-                            tma3(dst + (unsigned)(k * 32 * 16), mp, x0 + ch * EPT, R + G.o2 - (G.q2 - 1), (int)u,
-                                 A_FULL(ab));
-                            R += 32;
-                            if (R == T.lp) {
-                                R = 0;
-                                ++ch;
+                        // window chunk c reads flat rows f0 + c lp .. f0 + c lp + 32 fboxes: flat row P is
+                        // row P mod lp of group P / lp (32-row boxes never cross a group, lp and f0 being
+                        // multiples of 32), and c lp rows further is the same row one group (8 columns)
+                        // to the right
+                        for (int c = 0; c < T.kc; c++) {
+                            int ch = fch0 + c, R = fr0;
+                            for (int k = 0; k < T.fboxes; k++) {
+                                tma3(dst + (unsigned)((c * T.fboxes + k) * 32 * 16), mp, x0 + ch * EPT,
+                                     R + G.o2 - (G.q2 - 1), (int)u, A_FULL(ab));
+                                R += 32;
+                                if (R == T.lp) {
+                                    R = 0;
+                                    ++ch;
+                                }
                             }
                         }
                     } else {
@@ -321,7 +325,7 @@ conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtens
         // for every input plane and tile
         uint64_t* tab = reinterpret_cast<uint64_t*>(sm + lay.off_tab);
         for (int i = lane; i < T.steps; i += 32) {
-            const StepA sa = tc4_step(i, G.q2, T.kc, T.flat ? T.lp : T.rows);
+            const StepA sa = tc4_step(i, G.q2, T.kc, T.flat ? T.fboxes * 32 : T.rows);
             tab[i] = ((uint64_t)sa.lbo << 16) + (uint64_t)sa.start;
         }
         __syncwarp();

@@ -142,9 +142,9 @@ __global__ void __launch_bounds__(1024) grad_psf_kernel(GradPsfPlan g, GLayout l
 //    rs, rs + RS, ...
 //  * Per 4 columns of a row: one 16-byte load of x, 2 ceil((Q3 + 3) / 4) of the dY rows k2 + j2, and
 //    8 Q3 FMAs (Q3 + 3 window values against 4 x values, for both rows j2).
-//  * The next tile is copied (cp.async) while the current one is summed; tile sums are FP32 (at most
-//    1024 terms per thread and tile), accumulated across tiles in FP64 (shared memory), then reduced
-//    over rs in a fixed order.
+//  * The next tile is copied (cp.async) while the current one is summed; sums are FP32 over as many
+//    tiles as keep them at 1024 terms per thread at most, then added into FP64 sums (shared memory),
+//    which are reduced over rs in a fixed order.
 //  * One wave: q1 x chunks CTAs fill every SM's resident slots once (grad_psf_chunks).
 constexpr int QKW = 64;             // columns per tile
 constexpr int QTR = 16;             // rows per tile
@@ -229,6 +229,15 @@ __global__ void __launch_bounds__(512) grad_psf_q_kernel(GradPsfPlan g, int RS, 
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
 
+    // FP32 sums run over `flush` tiles (at most 1024 products each: 64 columns x ceil(16 / RS) rows per
+    // tile) before they are added to the FP64 sums: GB300 runs FP64 adds at a small fraction of the FP32
+    // FMA rate, and adding after every tile (22 adds per 1,408 FMAs for q3 = 11, RS = 16) kept the FP64
+    // pipe 61% busy against 35% for the FMAs
+    const int flush = max(1, QTR / ((QTR + RS - 1) / RS));
+    float acc[2][Q3];
+#pragma unroll
+    for (int q = 0; q < Q3; q++) acc[0][q] = acc[1][q] = 0.f;
+    int nacc = 0;
     int b = 0;
     if (ch < ntiles) stage(ch, 0);
     for (int64_t t = ch; t < ntiles; t += g.chunks, b ^= 1) {
@@ -242,9 +251,6 @@ __global__ void __launch_bounds__(512) grad_psf_q_kernel(GradPsfPlan g, int RS, 
         if (active) {
             const float* sx = smq + b * buf;
             const float* sd = sx + QTR * QXP;
-            float acc[2][Q3];
-#pragma unroll
-            for (int q = 0; q < Q3; q++) acc[0][q] = acc[1][q] = 0.f;
             for (int rr = rs; rr < QTR; rr += RS) {
                 const float* xr = sx + rr * QXP;
                 const float* da = sd + (rr + j2a) * DP;
@@ -282,11 +288,15 @@ __global__ void __launch_bounds__(512) grad_psf_q_kernel(GradPsfPlan g, int RS, 
                     }
                 }
             }
-            double* sa = s_acc + tid * 2 * Q3;
+            if (++nacc == flush || t + g.chunks >= ntiles) {
+                double* sa = s_acc + tid * 2 * Q3;
 #pragma unroll
-            for (int q = 0; q < Q3; q++) {
-                sa[q] += (double)acc[0][q];
-                sa[Q3 + q] += (double)acc[1][q];
+                for (int q = 0; q < Q3; q++) {
+                    sa[q] += (double)acc[0][q];
+                    sa[Q3 + q] += (double)acc[1][q];
+                    acc[0][q] = acc[1][q] = 0.f;
+                }
+                nacc = 0;
             }
         }
         __syncthreads();                                   // buffer b is overwritten by the next stage
