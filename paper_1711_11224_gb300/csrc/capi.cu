@@ -257,8 +257,6 @@ static bool tc4_config(const cdv_plan* P, const TcArgs& wide, bool flat, TcArgs&
     t.K = 8 * t.kc;
     t.kchunks = t.kc;
     t.steps = (g.q2 * t.kc + 1) / 2;
-    t.spst = t.kc;
-    t.nst = (t.steps + t.spst - 1) / t.spst;
     if (2 * t.rows + 1 >= (1 << 14)) return false;                 // descriptor offsets (16-byte units)
     t.tiles1 = ceil_div(g.b1, pc);
     t.tiles2 = ceil_div(g.b2, 128 * t.MT);
@@ -280,17 +278,16 @@ static bool tc4_config(const cdv_plan* P, const TcArgs& wide, bool flat, TcArgs&
             if (t.gfirst[c] < 0) t.gfirst[c] = gi;
             t.ngrp[c]++;
         }
-        for (int c = 0; c < 2; c++) {
+        for (int c = 0; c < 2; c++)
             if (t.gfirst[c] < 0) t.gfirst[c] = 0;
-            t.nblk[c] = ceil_div((int64_t)t.ngrp[c] * t.lp, 128 * t.MT);
-        }
+        t.nblk = (int)ceil_div((int64_t)(t.ngrp[0] + t.ngrp[1]) * t.lp, 128 * t.MT);
         // staged rows: per window chunk c, the 256 M rows shifted by c groups (c lp rows) plus q2 - 1
         // row shifts, in 32-row boxes; the rows between the chunks' windows are not loaded
         t.fboxes = ceil_div(128 * t.MT + g.q2 - 1, 32);
         if ((int64_t)t.kc * t.fboxes * 32 + g.q2 >= (1 << 14)) return false;     // descriptor offsets
         t.tiles2 = 1;
-        t.tiles3 = t.nblk[0] + t.nblk[1];
-        if ((int64_t)t.ngrp[0] * t.lp >= (1LL << 30) || (int64_t)t.ngrp[1] * t.lp >= (1LL << 30)) return false;
+        t.tiles3 = t.nblk;
+        if ((int64_t)(t.ngrp[0] + t.ngrp[1]) * t.lp >= (1LL << 30)) return false;
     }
     const int64_t ntiles = (int64_t)t.tiles1 * t.tiles2 * t.tiles3;
     if (ntiles > (1LL << 31) - 1) return false;
@@ -301,6 +298,19 @@ static bool tc4_config(const cdv_plan* P, const TcArgs& wide, bool flat, TcArgs&
         return false;
     t.grid = (int)std::min<int64_t>(ntiles, nsm);
     t.na = 2;
+    // template stages: as few per input plane as let two of them fit in shared memory (each stage
+    // costs the MMA warp a wait and a commit and the producer its copies: on ring3d 8 K steps per stage
+    // instead of 3 took split-BF16x3 from 7.56 to 6.61 ms per forward and adjoint, 16 instead of 3 BF16
+    // from 5.44 to 3.82), the K steps spread evenly over them
+    t.ns = 2;
+    int most = 0;
+    for (int sp = 1; sp <= t.steps; sp++) {
+        t.spst = sp;
+        if (tc4_smem_bytes(t) <= 220 * 1024) most = sp;
+    }
+    if (most == 0) return false;
+    t.nst = (t.steps + most - 1) / most;
+    t.spst = (t.steps + t.nst - 1) / t.nst;
     t.ns = 16;
     while (tc4_smem_bytes(t) > 220 * 1024 && t.ns > 2) t.ns--;
     return tc4_smem_bytes(t) <= 220 * 1024;
@@ -401,6 +411,21 @@ static cudaError_t tc_setup(cdv_plan* P)
     const bool w4 = P->tcf.w4 != 0;
     P->pitch_x1 = (P->m[2] + 4 + 7) / 8 * 8;
     P->pitch_r1 = (P->gf.b3 + 4 + 7) / 8 * 8;
+    if (w4) {
+        // The narrow kernel's window chunks past an input's last column read zero columns stored in the
+        // row pitch (its tensor maps span the whole pitch), not the TMA's out-of-bounds fill: loads
+        // that ran past the right edge made the CTAs of the last column groups 20-30% slower.
+        auto widen = [](int64_t& pitch, int64_t need) { pitch = std::max(pitch, (need + 7) / 8 * 8); };
+        int64_t need[2][2];
+        tc4_window_extent(P->tcf, need[0]);
+        tc4_window_extent(P->tca, need[1]);
+        widen(P->pitch_x, need[0][0]);
+        widen(P->pitch_x1, need[0][1]);
+        widen(P->pitch_r, need[1][0]);
+        widen(P->pitch_r1, need[1][1]);
+        P->tcf.sh_pitch = P->pitch_r;
+        P->tca.sh_pitch = P->pitch_x;
+    }
     const size_t xs = (size_t)P->m[0] * P->m[1] * P->pitch_x * es;
     const size_t rs = (size_t)P->gf.b1 * P->gf.b2 * P->pitch_r * es;
     for (int b = 0; b < 2; b++)
@@ -408,6 +433,9 @@ static cudaError_t tc_setup(cdv_plan* P)
             if (p < nprec) {
                 if ((e = P->alloc((unsigned char**)&P->xsh[b][p], xs)) != cudaSuccess) return e;
                 if ((e = P->alloc((unsigned char**)&P->rsh[b][p], rs)) != cudaSuccess) return e;
+                // the columns past each row's data stay zero (nothing writes them)
+                if (w4 && (e = cudaMemset(P->xsh[b][p], 0, xs)) != cudaSuccess) return e;
+                if (w4 && (e = cudaMemset(P->rsh[b][p], 0, rs)) != cudaSuccess) return e;
             } else {
                 P->xsh[b][p] = P->xsh[b][0];
                 P->rsh[b][p] = P->rsh[b][0];
@@ -449,18 +477,20 @@ static cudaError_t tc_setup(cdv_plan* P)
             // the forward reads X through 32-row boxes in the flat layout, else through two boxes of half the
             // staged rows; the adjoint reads R through the latter
             const int bx = P->tcf.flat ? 32 : P->tcf.rows / 2, br = P->tca.rows / 2;
-            if ((e = make_map(&P->map_x[2 * b + p], P, P->xsh[b][p], P->m[0], P->m[1], P->m[2], P->pitch_x, bx)) !=
+            // the narrow kernel's maps span the whole row pitch (zero columns past the data)
+            const int64_t wx = w4 ? P->pitch_x : P->m[2], wr = w4 ? P->pitch_r : P->gf.b3;
+            if ((e = make_map(&P->map_x[2 * b + p], P, P->xsh[b][p], P->m[0], P->m[1], wx, P->pitch_x, bx)) !=
                 cudaSuccess)
                 return e;
-            if ((e = make_map(&P->map_r[2 * b + p], P, P->rsh[b][p], P->gf.b1, P->gf.b2, P->gf.b3, P->pitch_r, br)) !=
+            if ((e = make_map(&P->map_r[2 * b + p], P, P->rsh[b][p], P->gf.b1, P->gf.b2, wr, P->pitch_r, br)) !=
                 cudaSuccess)
                 return e;
             if (!w4) continue;
-            if ((e = make_map(&P->map_x[4 + 2 * b + p], P, P->xsh1[b][p], P->m[0], P->m[1], P->m[2] + 4,
-                              P->pitch_x1, bx)) != cudaSuccess)
+            if ((e = make_map(&P->map_x[4 + 2 * b + p], P, P->xsh1[b][p], P->m[0], P->m[1], P->pitch_x1, P->pitch_x1,
+                              bx)) != cudaSuccess)
                 return e;
-            if ((e = make_map(&P->map_r[4 + 2 * b + p], P, P->rsh1[b][p], P->gf.b1, P->gf.b2, P->gf.b3 + 4,
-                              P->pitch_r1, br)) != cudaSuccess)
+            if ((e = make_map(&P->map_r[4 + 2 * b + p], P, P->rsh1[b][p], P->gf.b1, P->gf.b2, P->pitch_r1, P->pitch_r1,
+                              br)) != cudaSuccess)
                 return e;
         }
     for (int b = 0; b < 2; b++) {

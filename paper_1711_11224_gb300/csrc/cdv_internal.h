@@ -214,17 +214,18 @@ struct TcArgs {
     int pc;              // output planes per tile (a multiple of 32)
     int kc;              // 16-byte chunks of the window of 4 + q3 - 1 columns
     int steps;           // MMA K steps per input plane: ceil(q2 * kc / 2)
-    int spst;            // K steps per template stage (= kc: two template rows)
+    int spst;            // K steps per template stage
     int nst;             // template stages per input plane
     int64_t sh_pitch1;   // row pitch of the output shadows shifted by 4 columns
-    // forward only: M runs over (column group, row) of the groups of one shadow copy, rows padded to
-    // lp (a multiple of 32, >= b2); the input tile is staged in 32-row boxes
+    // forward only: M runs over (column group, row) of the groups of copy 0, then those of copy 1, rows
+    // padded to lp (a multiple of 32, >= b2); each window chunk is staged in 32-row boxes, each box from
+    // the copy its group belongs to
     int flat;
     int lp;
     int fboxes;          // 32-row boxes per window chunk of one staged input plane (one part)
     int ngrp[2];         // column groups per shadow copy
     int gfirst[2];       // first column group of each copy
-    int nblk[2];         // 256-row M blocks per copy
+    int nblk;            // 256-row M blocks over the groups of both copies
     // per-CTA tile lists: CTA b walks tlist[toff[b] .. toff[b + 1]), each tile {S1, s1_end, combo, 0}:
     // output planes [S1, s1_end) (S1 a multiple of 32) of M block `combo` (flat: index over the copies'
     // blocks; else row block * column groups + column group)
@@ -255,6 +256,7 @@ cudaError_t tc4_shadow1(const float* src, int64_t a1a2, int64_t a3, int64_t pitc
 // Balanced tile lists for the narrow kernel (host): fills the tile lists and the grid, returns the
 // modelled makespan in cycles; tc4_executed_macs counts the MMAs of those lists.
 double tc4_partition(TcArgs& t, int nsm, int pc, std::vector<int4>& list, std::vector<int>& off);
+void tc4_window_extent(const TcArgs& t, int64_t need[2]);
 double tc4_executed_macs(const TcArgs& t, const std::vector<int4>& list);
 
 // FFT comparator (fft.cu): cuFFT plans over the zero-padded grid of N_i >= m_i + 2p_i samples.

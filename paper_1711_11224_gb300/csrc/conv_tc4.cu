@@ -21,7 +21,7 @@ cudaError_t tc4_prepare(int kind)
 
 cudaError_t tc4_launch(const TcArgs& t, const CUtensorMap* maps, cudaStream_t s)
 {
-    if (!t.w4 || t.kc < 1 || t.spst != t.kc || t.nst * t.spst < t.steps || !t.tlist || !t.toff)
+    if (!t.w4 || t.kc < 1 || t.spst < 1 || t.nst * t.spst < t.steps || !t.tlist || !t.toff)
         return cudaErrorInvalidValue;
     if (t.var) return tc4_launch_var(t, maps, s);
     return tc4_launch_kinds<false>(t, maps, s);
@@ -101,6 +101,32 @@ cudaError_t tc4_shadow1(const float* src, int64_t a1a2, int64_t a3, int64_t pitc
 
 namespace cdv {
 
+// Farthest column (exclusive) that the window loads of a direction's tiles reach in each shadow copy:
+// column group g reads kc chunks from x = 4g + o3 - (q3 - 1), in copy 0 when x is a multiple of 8, else
+// in copy 1 (shifted right by 4 columns) from x + 4.
+void tc4_window_extent(const TcArgs& t, int64_t need[2])
+{
+    const ConvGeom& g = t.g;
+    need[0] = need[1] = 0;
+    for (int64_t s3 = 0; s3 < g.b3; s3 += kW4) {
+        const int64_t x = s3 + g.o3 - (g.q3 - 1);
+        const int c = (((x % 8) + 8) % 8) == 0 ? 0 : 1;
+        need[c] = std::max(need[c], x + 4 * c + 8 * (int64_t)t.kc);
+    }
+    if (t.flat && t.nblk > 0) {
+        // the last M block also stages rows past the last group (they hold no outputs), read from copy 1
+        const int64_t last = (int64_t)(t.nblk - 1) * kM * kMT + t.fboxes * 32 - 1;
+        const int64_t gl = last / t.lp - t.ngrp[0];
+        const int64_t x0 = 4 * (int64_t)t.gfirst[1] + g.o3 - (g.q3 - 1) + 4;
+        if (gl >= 0) need[1] = std::max(need[1], x0 + 8 * gl + 8 * (int64_t)t.kc);
+    }
+}
+
+// Weight of a tile's M tiles in the cycle model: a plane with one 128-row M tile costs about 0.67 of a
+// plane with two (measured per CTA on ring3d's forward), not half: the template stages and input boxes
+// of a plane are the same for one or two M tiles.
+static double tc4_mt_weight(int nmt) { return nmt == 1 ? 1.35 : (double)nmt; }
+
 // Modelled tensor-pipe cycles of the MMAs of one tile: each MMA costs about max(46, N / 2) cycles.
 static double tc4_tile_cycles(const TcArgs& t, const Tc4Tile& C)
 {
@@ -110,7 +136,7 @@ static double tc4_tile_cycles(const TcArgs& t, const Tc4Tile& C)
         C.mma_slots(t.g, u, k0, ns);
         c += std::max(46.0, kW4 * ns / 2.0);
     }
-    return c * t.steps * (double)C.mtiles(t);
+    return c * t.steps * tc4_mt_weight(C.mtiles(t));
 }
 
 // Tensor-pipe work of one launch of the narrow kernel, counting its loops: per tile and input plane,
@@ -139,7 +165,7 @@ double tc4_executed_macs(const TcArgs& t, const std::vector<int4>& list)
 double tc4_partition(TcArgs& t, int nsm, int pc, std::vector<int4>& list, std::vector<int>& off)
 {
     const ConvGeom& g = t.g;
-    const int ncombo = t.flat ? t.nblk[0] + t.nblk[1] : t.tiles2 * t.tiles3;
+    const int ncombo = t.flat ? t.nblk : t.tiles2 * t.tiles3;
     const int nb = (int)((g.b1 + 31) / 32);                  // 32-plane units
     // cycles of planes [32a, min(32e, b1)) of a combo with one M tile (a < e), cached
     std::vector<double> cost((size_t)nb * (nb + 1), -1.0);
@@ -152,12 +178,12 @@ double tc4_partition(TcArgs& t, int nsm, int pc, std::vector<int4>& list, std::v
             one.tiles3 = 1;
             const Tc4Tile C = Tc4Tile::make(one, make_int4(32 * a, (int)std::min<int64_t>(32 * (int64_t)e, g.b1), 0, 0));
             // one M tile of outputs (S2 = 0 with b2 of at least one row): scaled by the combo's M tiles below
-            c = tc4_tile_cycles(one, C) / std::max(1, C.mtiles(one));
+            c = tc4_tile_cycles(one, C) / tc4_mt_weight(std::max(1, C.mtiles(one)));
         }
         return c;
     };
-    std::vector<int> nmt(ncombo);
-    for (int j = 0; j < ncombo; j++) nmt[j] = Tc4Tile::make(t, make_int4(0, (int)g.b1, j, 0)).mtiles(t);
+    std::vector<double> nmt(ncombo);
+    for (int j = 0; j < ncombo; j++) nmt[j] = tc4_mt_weight(Tc4Tile::make(t, make_int4(0, (int)g.b1, j, 0)).mtiles(t));
     auto deal = [&](double T, std::vector<int4>* L, std::vector<int>* O) -> int {
         int cta = 0;
         double load = 0.0;

@@ -32,6 +32,10 @@ namespace {
 
 constexpr int kW4 = 4;           // output columns per tile
 constexpr int kSlots = 32;       // plane slots (N = kW4 x kSlots = 128)
+// Warps: 0 stages the input planes (TMA) and owns TMEM, 1 issues the MMAs, 2-9 run the epilogue, 10
+// stages the template (bulk copies); one thread issues all copies of each producer warp.
+constexpr int kThreads4 = 352;
+constexpr int kBWarp = 10;
 
 // K step i of an input plane: chunks (j2, c) of items 2i and 2i + 1 of the sequence over template
 // rows and window chunks (row-major; an odd total ends with a pad item whose B chunk is zero).  The
@@ -75,7 +79,7 @@ struct Tc4Smem {
         s.off_b = (size_t)t.na * t.nprec * s.a_bytes;
         s.off_bar = s.off_b + (size_t)t.ns * t.nprec * s.b_bytes;
         s.off_stage = s.off_bar + 512;
-        s.off_tab = s.off_stage + (size_t)(kThreads / 32 - 2) * 32 * kW4 * 4;   // 32 x 4 floats per epilogue warp
+        s.off_tab = s.off_stage + (size_t)8 * 32 * kW4 * 4;                    // 32 x 4 floats per epilogue warp
         s.total = s.off_tab + (size_t)t.steps * 8;                             // A descriptor offsets per K step
         return s;
     }
@@ -84,8 +88,9 @@ struct Tc4Smem {
 // One tile of the narrow kernel: output planes [S1, s1_end) (S1 a multiple of 32), rows
 // [S2, S2 + 256), columns [S3, S3 + 4), input planes [ulo, uhi]; par = the shadow copy in which the
 // window of the tile starts on a chunk.
-// Flat tiles (forward): M row f of block f0 is row f mod lp of column group gfirst + 2 (f / lp) of the
-// tile's shadow copy; rows f >= nf (or rows >= b2) hold no outputs.
+// Flat tiles (forward): M row f (of block f0 .. f0 + 255) is row f mod lp of flat group G = f / lp;
+// groups 0 .. ngrp0 - 1 are the column groups gfirst0 + 2i of copy 0, the next ngrp1 those of copy 1;
+// rows f >= nf (or rows >= b2) hold no outputs.
 struct Tc4Tile {
     int64_t S1, S2, S3, s1_end, ulo, uhi;
     int par;
@@ -104,11 +109,11 @@ struct Tc4Tile {
         const int64_t hi = c.s1_end - 1 + G.o1;
         c.uhi = hi < G.a1 - 1 ? hi : G.a1 - 1;
         if (T.flat) {
-            c.par = t3 < T.nblk[0] ? 0 : 1;
-            c.f0 = (int64_t)(t3 - (c.par ? T.nblk[0] : 0)) * kM * kMT;
-            c.nf = (int64_t)T.ngrp[c.par] * T.lp;
+            c.par = 0;
+            c.f0 = (int64_t)t3 * kM * kMT;
+            c.nf = (int64_t)(T.ngrp[0] + T.ngrp[1]) * T.lp;
             c.S2 = 0;
-            c.S3 = (int64_t)T.gfirst[c.par] * kW4;
+            c.S3 = 0;
         } else {
             c.S2 = (int64_t)t2 * kM * kMT;
             c.S3 = (int64_t)t3 * kW4;
@@ -152,7 +157,7 @@ struct Tc4Tile {
 };
 
 template <int KIND, bool VAR>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads4, 1)
 conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtensorMap m00,
                 const __grid_constant__ CUtensorMap m01, const __grid_constant__ CUtensorMap m10,
                 const __grid_constant__ CUtensorMap m11, const __grid_constant__ CUtensorMap s00,
@@ -243,8 +248,10 @@ conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtens
         atomicExch(T.err, (int)CDV_ERR_TIMEOUT);
     };
 
-    if (run && warp == 0 && lane == 0) {
-        // ---------------- TMA producer
+    if (run && (warp == 0 || warp == kBWarp) && lane == 0) {
+        // ---------------- producers: input planes (warp 0) and template stages (warp 10), each walking
+        // the same tiles and input planes
+        const bool doA = warp == 0, doB = warp == kBWarp;
         int bs = 0, it = 0, nb = 0;
         unsigned bph = 0;
         int a_uses[2] = {0, 0};
@@ -256,7 +263,12 @@ conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtens
             const int64_t v0 = C.S2 + G.o2 - (G.q2 - 1);
             const CUtensorMap* mh = C.par ? (sel ? &s10 : &s00) : (sel ? &m10 : &m00);
             const CUtensorMap* ml = C.par ? (sel ? &s11 : &s01) : (sel ? &m11 : &m01);
+            const CUtensorMap* sh = sel ? &s10 : &s00;               // flat tiles: copy 1 (copy 0 is mh, ml)
+            const CUtensorMap* sl = sel ? &s11 : &s01;
+            // flat tiles: TMA column of window chunk 0 of the first group of each copy (multiples of 8)
+            const int xg[2] = {4 * T.gfirst[0] + (int)G.o3 - (G.q3 - 1), 4 * T.gfirst[1] + (int)G.o3 - (G.q3 - 1) + 4};
             for (int64_t u = C.ulo; u <= C.uhi && !*sflag; ++u, ++it) {
+                if (doA) {
                 const int ab = it % T.na;
                 if (!mbar_wait(A_EMPTY(ab), (unsigned)(((it / T.na) & 1) ^ 1), T.wait_cycles)) { fail(); break; }
                 mbar_expect_tx(A_FULL(ab), (unsigned)(NPREC * lay.a_bytes));
@@ -265,19 +277,21 @@ conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtens
                     const CUtensorMap* mp = p ? ml : mh;
                     const unsigned dst = su32(sA + ((size_t)ab * NPREC + p) * lay.a_bytes);
                     if (T.flat) {
-                        // window chunk c reads flat rows f0 + c lp .. f0 + c lp + 32 fboxes: flat row P is
-                        // row P mod lp of group P / lp (32-row boxes never cross a group, lp and f0 being
-                        // multiples of 32), and c lp rows further is the same row one group (8 columns)
-                        // to the right
+                        // window chunk c: the 32 fboxes rows from M row f0, each 32-row box (boxes never
+                        // cross a group, lp and f0 being multiples of 32) read from the copy of its flat
+                        // group, 8c columns right of the start of that group's window
                         for (int c = 0; c < T.kc; c++) {
-                            int ch = fch0 + c, R = fr0;
+                            int gg = fch0, R = fr0;
                             for (int k = 0; k < T.fboxes; k++) {
-                                tma3(dst + (unsigned)((c * T.fboxes + k) * 32 * 16), mp, x0 + ch * EPT,
-                                     R + G.o2 - (G.q2 - 1), (int)u, A_FULL(ab));
+                                const int cp = gg >= T.ngrp[0] ? 1 : 0;
+                                const CUtensorMap* mb = cp ? (p ? sl : sh) : mp;
+                                tma3(dst + (unsigned)((c * T.fboxes + k) * 32 * 16), mb,
+                                     xg[cp] + (gg - (cp ? T.ngrp[0] : 0) + c) * EPT, R + G.o2 - (G.q2 - 1), (int)u,
+                                     A_FULL(ab));
                                 R += 32;
                                 if (R == T.lp) {
                                     R = 0;
-                                    ++ch;
+                                    ++gg;
                                 }
                             }
                         }
@@ -288,25 +302,29 @@ conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtens
                                      (int)(v0 + h * half), (int)u, A_FULL(ab));
                     }
                 }
-                int k0, nsl;
-                C.mma_slots(G, u, k0, nsl);
-                // rotation: the j1 = 0 plane u - o1 sits in slot r; slot pair g holds doubled-sequence
-                // entries 2g + 32 - r and 2g + 33 - r, i.e. version (r & 1), group gs + g
-                const int r = (int)((((u - G.o1) % kSlots) + kSlots) % kSlots);
-                const int ver = r & 1;
-                const int gs = ver ? (31 - r) / 2 : 16 - r / 2;
-                const int g0 = k0 / 2, ng = nsl / 2;
-                for (int t = 0; t < T.nst; t++) {
-                    if (!mbar_wait(B_EMPTY(bs), bph ^ 1, T.wait_cycles)) { fail(); break; }
-                    mbar_expect_tx(B_FULL(bs), (unsigned)(NPREC * ng * gbytes));
-                    for (int p = 0; p < NPREC; p++) {
-                        const unsigned char* src = reinterpret_cast<const unsigned char*>(T.bt[p]) +
-                                                   (((size_t)t * 2 + ver) * kSlots + (size_t)(gs + g0)) * gbytes;
-                        const unsigned dst = su32(sB + ((size_t)bs * NPREC + p) * lay.b_bytes) + (unsigned)(g0 * gbytes);
-                        bulk_g2s(dst, src, (unsigned)(ng * gbytes), B_FULL(bs));
+                }
+                if (doB) {
+                    int k0, nsl;
+                    C.mma_slots(G, u, k0, nsl);
+                    // rotation: the j1 = 0 plane u - o1 sits in slot r; slot pair g holds doubled-sequence
+                    // entries 2g + 32 - r and 2g + 33 - r, i.e. version (r & 1), group gs + g
+                    const int r = (int)((((u - G.o1) % kSlots) + kSlots) % kSlots);
+                    const int ver = r & 1;
+                    const int gs = ver ? (31 - r) / 2 : 16 - r / 2;
+                    const int g0 = k0 / 2, ng = nsl / 2;
+                    for (int t = 0; t < T.nst; t++) {
+                        if (!mbar_wait(B_EMPTY(bs), bph ^ 1, T.wait_cycles)) { fail(); break; }
+                        mbar_expect_tx(B_FULL(bs), (unsigned)(NPREC * ng * gbytes));
+                        for (int p = 0; p < NPREC; p++) {
+                            const unsigned char* src = reinterpret_cast<const unsigned char*>(T.bt[p]) +
+                                                       (((size_t)t * 2 + ver) * kSlots + (size_t)(gs + g0)) * gbytes;
+                            const unsigned dst =
+                                su32(sB + ((size_t)bs * NPREC + p) * lay.b_bytes) + (unsigned)(g0 * gbytes);
+                            bulk_g2s(dst, src, (unsigned)(ng * gbytes), B_FULL(bs));
+                        }
+                        ++nb;
+                        if (++bs == T.ns) { bs = 0; bph ^= 1; }
                     }
-                    ++nb;
-                    if (++bs == T.ns) { bs = 0; bph ^= 1; }
                 }
             }
         }
@@ -384,7 +402,7 @@ conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtens
 
     // ---------------- epilogue (warps 2..9): one output row per thread, warpgroup g owns M tile g
     float loc = 0.f, loc_a = 0.f, loc_x = 0.f, loc_sy = 0.f;
-    if (warp >= 2) {
+    if (warp >= 2 && warp < kBWarp) {
         const int mt = (warp - 2) >> 2;
         const int quarter = warp & 3;
         float* stg = reinterpret_cast<float*>(sm + lay.off_stage) + (warp - 2) * 32 * kW4;
@@ -404,7 +422,9 @@ conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtens
                 if (f >= (int)C.nf) return false;
                 const int gg = f / T.lp;
                 s2 = f - gg * T.lp;
-                s3 += 8 * gg;                                         // groups of one copy are 8 columns apart
+                // flat group gg: copy 0's groups, then copy 1's; the groups of one copy are 8 columns apart
+                const int cp = gg >= T.ngrp[0] ? 1 : 0;
+                s3 = 4 * (int64_t)T.gfirst[cp] + 8 * (int64_t)(gg - (cp ? T.ngrp[0] : 0)) + c;
             }
             if (s2 >= G.b2 || s3 >= G.b3) return false;
             const int64_t row = s1 * G.b2 + s2;
@@ -564,7 +584,7 @@ conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtens
 
     // ---------------- block partials of the norms, teardown (as in conv_tc.cuh)
     constexpr int NR = VAR ? 4 : 1;
-    __shared__ double s_red[NR][kThreads / 32];
+    __shared__ double s_red[NR][kThreads4 / 32];
     if (role == ROLE_FWD_INIT || role == ROLE_FWD_TRIAL || role == ROLE_ADJ_TRIAL) {
         double v[4] = {(double)loc, (double)loc_a, (double)loc_x, (double)loc_sy};
 #pragma unroll
@@ -579,7 +599,7 @@ conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtens
     if (tid == 0 && (role == ROLE_FWD_INIT || role == ROLE_FWD_TRIAL || role == ROLE_ADJ_TRIAL)) {
         double t[NR];
         for (int k = 0; k < NR; k++) t[k] = 0.0;
-        for (int i = 0; i < kThreads / 32; i++)
+        for (int i = 0; i < kThreads4 / 32; i++)
             for (int k = 0; k < NR; k++) t[k] += s_red[k][i];
         double* part = (role == ROLE_ADJ_TRIAL) ? T.ctx.part_m : T.ctx.part_f;
         part[blockIdx.x] = t[0];
@@ -616,10 +636,10 @@ static cudaError_t tc4_launch_kinds(const TcArgs& t, const CUtensorMap* m, cudaS
     const dim3 grid((unsigned)t.grid);
     switch (t.kind) {
     case CDV_MODE_BF16:
-        conv_tc4_kernel<CDV_MODE_BF16, VAR><<<grid, kThreads, smem, s>>>(t, m[0], m[1], m[2], m[3], m[4], m[5], m[6], m[7]);
+        conv_tc4_kernel<CDV_MODE_BF16, VAR><<<grid, kThreads4, smem, s>>>(t, m[0], m[1], m[2], m[3], m[4], m[5], m[6], m[7]);
         break;
     case CDV_MODE_SPLIT_BF16X3:
-        conv_tc4_kernel<CDV_MODE_SPLIT_BF16X3, VAR><<<grid, kThreads, smem, s>>>(t, m[0], m[1], m[2], m[3], m[4], m[5], m[6],
+        conv_tc4_kernel<CDV_MODE_SPLIT_BF16X3, VAR><<<grid, kThreads4, smem, s>>>(t, m[0], m[1], m[2], m[3], m[4], m[5], m[6],
                                                                                  m[7]);
         break;
     default: return cudaErrorInvalidValue;
