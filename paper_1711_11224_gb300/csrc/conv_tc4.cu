@@ -21,7 +21,7 @@ cudaError_t tc4_prepare(int kind)
 
 cudaError_t tc4_launch(const TcArgs& t, const CUtensorMap* maps, cudaStream_t s)
 {
-    if (!t.w4 || t.kc < 1 || t.spst < 1 || t.nst * t.spst < t.steps || !t.tlist || !t.toff)
+    if (!t.w4 || t.kc < 1 || t.spst < 1 || t.na != 2 || t.nst * t.spst < t.steps || !t.tlist || !t.toff)
         return cudaErrorInvalidValue;
     if (t.var) return tc4_launch_var(t, maps, s);
     return tc4_launch_kinds<false>(t, maps, s);

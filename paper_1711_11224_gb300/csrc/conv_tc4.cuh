@@ -210,10 +210,10 @@ conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtens
     unsigned char* sB = sm + lay.off_b;
     const unsigned bar0 = su32(sm + lay.off_bar);
     auto A_FULL = [&](int i) { return bar0 + 8u * i; };
+    // input buffer i free again = the MMAs of the plane that used it (and of partial i) complete
     auto A_EMPTY = [&](int i) { return bar0 + 8u * (2 + i); };
     auto B_FULL = [&](int i) { return bar0 + 8u * (4 + i); };
     auto B_EMPTY = [&](int i) { return bar0 + 8u * (20 + i); };
-    auto ACC_FULL = [&](int i) { return bar0 + 8u * (36 + i); };
     auto ACC_FREE = [&](int i) { return bar0 + 8u * (38 + i); };
     const unsigned DRAIN = bar0 + 8u * 40;
     unsigned* tslot = reinterpret_cast<unsigned*>(sm + lay.off_bar + 384);
@@ -335,7 +335,8 @@ conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtens
             mbar_wait(B_FULL(idx % T.ns), (unsigned)((idx / T.ns) & 1));
         }
     } else if (run && warp == 1) {
-        // ---------------- MMA issuer (whole warp, one elected lane issues)
+        // ---------------- MMA issuer (whole warp, one elected lane issues: the descriptors stay
+        // warp-uniform; a loop on one lane ran 30% slower)
         const unsigned sA16 = (su32(sA) & 0x3FFFFu) >> 4, sB16 = (su32(sB) & 0x3FFFFu) >> 4;
         const unsigned a_part16 = (unsigned)(lay.a_bytes >> 4), b_part16 = (unsigned)(lay.b_bytes >> 4);
         const uint64_t db0 = sdesc(0, 128, (unsigned)gbytes);
@@ -355,10 +356,9 @@ conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtens
             const Tc4Tile C = Tc4Tile::make(T, T.tlist[kt]);
             const int nmt = C.mtiles(T);
             for (int64_t u = C.ulo; u <= C.uhi; ++u, ++it) {
-                const int b = it & 1;
-                const int ab = it % T.na;
+                const int b = it & 1;                // accumulator buffer and input-plane buffer (na = 2)
                 bool w = it < 2 || mbar_wait(ACC_FREE(b), (unsigned)(((it >> 1) - 1) & 1), T.wait_cycles);
-                w = w && mbar_wait(A_FULL(ab), (unsigned)((it / T.na) & 1), T.wait_cycles);
+                w = w && mbar_wait(A_FULL(b), (unsigned)((it >> 1) & 1), T.wait_cycles);
                 if (!__all_sync(0xffffffffu, w && !*sflag)) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 int k0, nsl;
@@ -366,7 +366,7 @@ conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtens
                 const unsigned n = (unsigned)(kW4 * nsl);
                 const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((unsigned)(kM >> 4) << 24);
                 const unsigned d = tmem + (unsigned)(b * kNT + k0 * kW4);
-                const unsigned a_hi = sA16 + (unsigned)(ab * NPREC) * a_part16;
+                const unsigned a_hi = sA16 + (unsigned)(b * NPREC) * a_part16;
                 const unsigned a_lo = a_hi + (unsigned)(NPREC - 1) * a_part16;
                 unsigned acc = 0;
                 for (int t = 0; t < T.nst; t++) {
@@ -391,8 +391,9 @@ conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtens
                     if (++bs == T.ns) { bs = 0; bph ^= 1; }
                 }
                 if (!ok) break;
-                mma_commit_elect(A_EMPTY(ab));
-                mma_commit_elect(ACC_FULL(b));
+                // one commit tells both the producer (input buffer b free) and the epilogue (partial b
+                // complete)
+                mma_commit_elect(A_EMPTY(b));
             }
         }
         if (!ok && lane == 0) fail();
@@ -524,7 +525,7 @@ conv_tc4_kernel(const __grid_constant__ TcArgs T, const __grid_constant__ CUtens
                         if (locate(C, sdone, k, idx, i0, i1)) pre[k] = operand(idx);
                     }
                 }
-                bool w = mbar_wait(ACC_FULL(b), (unsigned)((it >> 1) & 1), T.wait_cycles);
+                bool w = mbar_wait(A_EMPTY(b), (unsigned)((it >> 1) & 1), T.wait_cycles);   // plane it's MMAs done
                 w = __all_sync(0xffffffffu, w && !*sflag);
                 if (!w) {
                     ok = false;
