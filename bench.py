@@ -732,6 +732,14 @@ def run_batch(args):
         g = torch.tensor([gmac], device=dev, dtype=torch.float64)
         dist.all_reduce(g, op=dist.ReduceOp.SUM)
         gmac = float(g.item())
+    # the same run through common trial slots of batched launches (path="general"), for comparison
+    bp.iterate(Ys, Xs, K=K, x0="crop", path="general")
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    _, reps_slot = bp.iterate(Ys, Xs, K=K, x0="crop", path="general", use_graph=not args.no_graph)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_slot = ev0.elapsed_time(ev1) / 1e3
     # the plain form: each volume alone through cdv_iterate (general path, its own graph), back to back
     seq = 0.0
     for P, Y, X in zip(probs, Ys, Xs):
@@ -748,10 +756,12 @@ def run_batch(args):
             seq += e0.elapsed_time(e1) / 1e3
     nconv = len(probs) * (1 + 2 * K)
     ng = len({P.H.shape[-1] for P in probs})          # one batched launch per template width per convolution
-    trials = max(r["trials"] for r in reps)
-    # x0, state, forward per width, decision, then per trial slot: adjoint and forward per width, decision,
-    # loop condition; finalize
-    launches = 1 + 1 + ng + 1 + trials * (2 * ng + 2) + 1
+    trials = max(r["trials"] for r in reps_slot)
+    # persistent run: x0, state, the persistent kernel, finalize (and three memsets).  Slot path: x0, state,
+    # forward per width, decision, then per trial slot: adjoint and forward per width, decision, loop
+    # condition; finalize
+    launches = 4
+    launches_slot = 1 + 1 + ng + 1 + trials * (2 * ng + 2) + 1
     out = {"metric": METRIC, "value": gmac / t, "unit": "GMAC/s", "n_gpus": ws, "steps": K,
            "warmup": args.warmup, "ms_per_step": t * 1e3 / max(1, acc), "higher_is_better": True,
            "scaling": "strong" if ws > 1 else "weak",
@@ -760,6 +770,10 @@ def run_batch(args):
                       "K_per_call": K, "accepted_min": acc, "all_ok": all(r["status"] == "CDV_OK" for r in reps),
                       "l2": "inputs larger than L2 (%.0f MB of Y)" % (sum(P.Y.nbytes for P in probs) / 1e6)},
            "iters_per_s": acc / t, "gpu_launches": launches,
+           "run": "one persistent launch for every volume's whole run (cdv_batch_iterate, path persistent)",
+           "slot_path": {"value": sum(r["gmac"] for r in reps_slot) / t_slot, "unit": "GMAC/s", "seconds": t_slot,
+                         "gpu_launches": launches_slot,
+                         "call": "cdv_batch_iterate, path general: common trial slots of batched launches"},
            "sequential_plain": {"value": sum(r["gmac"] for r in reps) / seq, "unit": "GMAC/s", "seconds": seq,
                                 "call": "cdv_iterate per volume (general path), back to back"},
            "batched_speedup": seq / t, "convolutions": nconv, "clocks": clk.summary()}

@@ -235,9 +235,11 @@ typedef struct {
 typedef enum {
     CDV_PATH_AUTO = 0,      /* the single-CTA path when the problem fits in one SM, else the general one */
     CDV_PATH_GENERAL = 1,   /* per-step forward/adjoint launches over the whole GPU (CUDA graph) */
-    CDV_PATH_SMALL = 2      /* one CTA holds the whole problem in shared memory and runs all K steps
+    CDV_PATH_SMALL = 2,     /* one CTA holds the whole problem in shared memory and runs all K steps
                                in one launch; CDV_ERR_UNSUPPORTED if it does not fit (template width
                                along the contiguous axis <= 15, about 200 KB of state) */
+    CDV_PATH_PERSISTENT = 3 /* batched solver only (its default, as CDV_PATH_AUTO): one persistent launch
+                               runs every volume's whole run; cdv_iterate answers CDV_ERR_UNSUPPORTED */
 } cdv_iter_path;
 
 /* Fill `o` with the defaults above. */
@@ -291,10 +293,15 @@ cdv_status cdv_richardson_lucy(cdv_plan* plan, const float* Y, float* X, int K, 
 /*
  * Batched solver: `count` independent problems, volume i with n axes of
  * m[i*n + a] samples and template half-widths p[i*n + a], all iterated
- * together (Steps 1-3 per volume, each with its own step rule).  One trial
- * slot runs batched launches whose work lists hold the tiles of every volume
- * (one launch per template width along the contiguous axis), and the whole
- * K-step run is replayed as one CUDA graph.  With autotune != 0 the tile shape
+ * together (Steps 1-3 per volume, each with its own step rule).  By default
+ * (path CDV_PATH_AUTO or CDV_PATH_PERSISTENT) one persistent launch runs every
+ * volume's whole run: its CTAs take the FP32-engine tiles of any volume whose
+ * current phase (initial forward, adjoint trial, forward trial) has tiles left,
+ * and the CTA that completes a phase runs that volume's FP64 step rule, so the
+ * volumes advance independently.  With CDV_PATH_GENERAL the volumes advance
+ * through common trial slots of batched launches whose work lists hold the
+ * tiles of every volume (one launch per template width along the contiguous
+ * axis).  Either run is replayed as one CUDA graph (use_graph = 1).  With autotune != 0 the tile shape
  * of each volume and direction is chosen by timing the candidates at plan
  * creation (results cached per process); iterates do not depend on the tile
  * shape and equal those of cdv_iterate on each volume alone.  CDV_MODE_FP32
@@ -315,7 +322,10 @@ cdv_status cdv_batch_set_psfs(cdv_batch* b, const float* const* H, void* stream)
  * X[i] (device, m_i; x_0 per policy in, x_K out).  `reports`, if not NULL,
  * points to `count` reports (their f_hist/delta_hist arrays optional) and the
  * call then synchronises `stream`.  The captured graph is reused while the
- * arrays, K and the options stay the same.
+ * arrays, K and the options stay the same.  CDV_ERR_UNSUPPORTED for path
+ * CDV_PATH_SMALL; with reports, CDV_ERR_TIMEOUT if a CTA of the persistent run
+ * found no tile to take for the wait budget (about 0.5 s: a fault of the run,
+ * not expected).
  */
 cdv_status cdv_batch_iterate(cdv_batch* b, const float* const* Y, float* const* X, int K, const cdv_iter_opts* opts,
                              cdv_iter_report* reports, void* stream);

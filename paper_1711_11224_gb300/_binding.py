@@ -21,7 +21,7 @@ STATUS = {
 }
 MODES = {"fp32": 0, "bf16": 1, "tf32": 2, "split3": 3, "fft": 4, "separable": 5}
 X0 = {"given": 0, "crop": 1, "zero": 2}
-PATHS = {"auto": 0, "general": 1, "small": 2}
+PATHS = {"auto": 0, "general": 1, "small": 2, "persistent": 3}
 
 # Every symbol include/cdv.h declares (checked by the tests).
 EXPORTS = [

@@ -1036,6 +1036,8 @@ cdv_status cdv_iterate(cdv_plan* plan, const float* Y, float* X, int K, const cd
     if (!(o.beta > 0.0 && o.beta < 1.0)) return fail(CDV_ERR_INVALID_ARG, "beta = %g", o.beta);
     if (o.max_halvings < 0 || o.max_rejects < 0 || o.max_rejects > 1 << 20)
         return fail(CDV_ERR_INVALID_ARG, "max_halvings/max_rejects");
+    if (o.path == CDV_PATH_PERSISTENT)
+        return fail(CDV_ERR_UNSUPPORTED, "CDV_PATH_PERSISTENT is the batched solver's path (cdv_batch_iterate)");
     if (o.path < CDV_PATH_AUTO || o.path > CDV_PATH_SMALL) return fail(CDV_ERR_INVALID_ARG, "path = %d", o.path);
     if (!(o.tikhonov >= 0.0 && o.tikhonov < 1e300)) return fail(CDV_ERR_INVALID_ARG, "tikhonov = %g", o.tikhonov);
     if (!(o.armijo >= 0.0 && o.armijo < 1.0)) return fail(CDV_ERR_INVALID_ARG, "armijo = %g", o.armijo);

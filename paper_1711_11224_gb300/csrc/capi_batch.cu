@@ -1,13 +1,18 @@
 // Batched solver: many independent volumes, each with its own size and
 // template, iterated together (Steps 1-3 applied to every volume).
 //
-// All volumes advance in lockstep through the same trial slots; one slot is
-// one batched adjoint launch and one batched forward launch per template width
-// present (each CTA of such a launch computes one tile of one volume, chosen
-// from a work list ordered largest volume first), plus one batched decision
-// launch (one block per volume, each with its own FP64 step rule).  The whole
-// K-step run is one CUDA graph (a WHILE loop over trial slots that ends when
-// every volume is done), captured once and replayed.  Per-volume tile
+// By default (CDV_PATH_AUTO or CDV_PATH_PERSISTENT) one persistent launch runs
+// the whole K-step run of every volume (conv_fp32_persist.cu): its CTAs take
+// tiles of any volume whose current phase has tiles left, and the CTA that
+// completes a phase runs that volume's step rule, so each volume advances at
+// its own pace.  With CDV_PATH_GENERAL all volumes advance in lockstep through
+// the same trial slots instead; one slot is one batched adjoint launch and one
+// batched forward launch per template width present (each CTA of such a launch
+// computes one tile of one volume, chosen from a work list ordered largest
+// volume first), plus one batched decision launch (one block per volume, each
+// with its own FP64 step rule), and the K-step run is a WHILE loop over trial
+// slots that ends when every volume is done.  Either run is one CUDA graph,
+// captured once and replayed.  Per-volume tile
 // shapes come from a timing autotuner whose results are cached per process
 // (keyed by device, geometry and direction); the arithmetic of every output
 // sample does not depend on the tile shape, so a volume's iterates are
@@ -88,6 +93,14 @@ struct cdv_batch {
     BatchVolCtx* d_ctx = nullptr;
     int2* d_items_f = nullptr;
     int2* d_items_a = nullptr;
+    // persistent run: scan order, per-volume phase words and tile counters, retired count, error word
+    int* d_order = nullptr;
+    int2* d_ntiles = nullptr;
+    unsigned long long* d_word = nullptr;
+    int* d_tiles_done = nullptr;
+    int* d_flags = nullptr;             // [0] volumes retired, [1] error
+    size_t psmem = 0;
+    int pgrid = 0;
     cudaStream_t cap = nullptr;
     // one stream per template-width group: the groups' launches of a trial slot run side by side
     // (captured as parallel graph branches), joined before the decision
@@ -99,6 +112,7 @@ struct cdv_batch {
     std::vector<const float*> key_y;
     std::vector<float*> key_x;
     int key_K = -1;
+    int key_persist = -1;
     cdv_iter_opts key_o{};
     bool key_valid = false;
 
@@ -292,6 +306,25 @@ cdv_status cdv_batch_plan_create(cdv_batch** out, int count, int n, const int64_
         if (e == cudaSuccess) B->gdone.push_back(d);
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming);
+    // persistent run: volumes scanned in the work lists' order, shared memory for any tile of the batch
+    if (e == cudaSuccess) e = B->alloc(&B->d_order, count);
+    if (e == cudaSuccess) e = B->alloc(&B->d_word, count);
+    if (e == cudaSuccess) e = B->alloc(&B->d_tiles_done, count);
+    if (e == cudaSuccess) e = B->alloc(&B->d_flags, 2);
+    if (e == cudaSuccess) e = cudaMemcpy(B->d_order, order.data(), count * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = B->alloc(&B->d_ntiles, count);
+    if (e == cudaSuccess) {
+        std::vector<int2> nt(count);
+        for (int k = 0; k < count; k++) nt[k] = make_int2(B->v[order[k]].tf.grid, B->v[order[k]].ta.grid);
+        e = cudaMemcpy(B->d_ntiles, nt.data(), count * sizeof(int2), cudaMemcpyHostToDevice);
+    }
+    B->psmem = 512 * sizeof(double);
+    for (int i = 0; i < count; i++) B->psmem = std::max(B->psmem, std::max(B->v[i].tf.smem, B->v[i].ta.smem));
+    if (e == cudaSuccess) e = conv_fp32_persist_prepare();
+    if (e == cudaSuccess) {
+        B->pgrid = conv_fp32_persist_grid(B->psmem);
+        if (B->pgrid < 1) e = cudaErrorInvalidConfiguration;
+    }
     if (e == cudaSuccess) e = B->alloc(&B->d_items_f, items_f.size());
     if (e == cudaSuccess) e = B->alloc(&B->d_items_a, items_a.size());
     if (e == cudaSuccess)
@@ -428,6 +461,23 @@ static cdv_status batch_phase(void* vctx, int phase, bool loop, unsigned long lo
     return CDV_OK;
 }
 
+// The persistent run: reset the phase words and counters, x0 and the states, one launch for every
+// volume's whole run, then x_K into the caller's arrays.
+static cdv_status batch_persist_enqueue(cdv_batch* b, int K, const cdv_iter_opts& o, cudaStream_t s)
+{
+    BCUDA(cudaMemsetAsync(b->d_word, 0, b->count * sizeof(unsigned long long), s), "reset phases");
+    BCUDA(cudaMemsetAsync(b->d_tiles_done, 0, b->count * sizeof(int), s), "reset counters");
+    BCUDA(cudaMemsetAsync(b->d_flags, 0, 2 * sizeof(int), s), "reset flags");
+    BCUDA(launch_batch_x0(b->d_ctx, b->count, o.x0_policy, s), "x0");
+    BCUDA(launch_batch_state_init(b->d_ctx, b->count, o.delta0 > 0.0 ? o.delta0 : 0.0, o.beta, o.max_halvings,
+                                  o.max_rejects, K, kBatchHist, s), "state");
+    BatchPersist P{b->d_fwd_init, b->d_fwd_trial, b->d_adj_trial, b->d_ctx, b->d_order, b->d_ntiles, b->d_word, b->d_tiles_done,
+                   b->d_flags, b->d_flags + 1, b->count, K + o.max_rejects + 1, kTcWaitCycles};
+    BCUDA(conv_fp32_persist_launch(P, b->pgrid, b->psmem, s), "persistent run");
+    BCUDA(launch_batch_finalize(b->d_ctx, b->count, s), "finalize");
+    return CDV_OK;
+}
+
 static cdv_status batch_enqueue(cdv_batch* b, int K, const cdv_iter_opts& o, cudaStream_t s)
 {
     BatchRun R{b, K, o};
@@ -452,11 +502,15 @@ cdv_status cdv_batch_iterate(cdv_batch* b, const float* const* Y, float* const* 
         return bfail(CDV_ERR_INVALID_ARG, "iteration options");
     if (o.tikhonov != 0.0 || o.armijo != 0.0 || o.bb != 0)
         return bfail(CDV_ERR_UNSUPPORTED, "the batched solver runs the plain step rule (tikhonov = armijo = bb = 0)");
+    if (o.path == CDV_PATH_SMALL || o.path < CDV_PATH_AUTO || o.path > CDV_PATH_PERSISTENT)
+        return bfail(o.path == CDV_PATH_SMALL ? CDV_ERR_UNSUPPORTED : CDV_ERR_INVALID_ARG,
+                     "path = %d: the batched solver runs CDV_PATH_PERSISTENT (AUTO) or CDV_PATH_GENERAL", o.path);
+    const int persist = o.path != CDV_PATH_GENERAL;
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<const float*> ky(Y, Y + b->count);
     std::vector<float*> kx(X, X + b->count);
     const bool same = b->key_valid && ky == b->key_y && kx == b->key_x && K == b->key_K &&
-                      memcmp(&o, &b->key_o, sizeof o) == 0;
+                      persist == b->key_persist && memcmp(&o, &b->key_o, sizeof o) == 0;
     if (!same || !o.use_graph) {
         BCUDA(cudaStreamSynchronize(s), "sync before table update");
         cdv_status st = batch_tables(b, Y, X);
@@ -471,24 +525,44 @@ cdv_status cdv_batch_iterate(cdv_batch* b, const float* const* Y, float* const* 
             b->key_valid = false;
             BatchRun R{b, K, o};
             cudaGraph_t gr = nullptr;
-            cdv_status st = build_loop_graph(b->cap, batch_phase, &R, &gr);
+            cdv_status st = CDV_OK;
+            if (persist) {
+                BCUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+                st = batch_persist_enqueue(b, K, o, b->cap);
+                cudaGraph_t tmp = nullptr;
+                const cudaError_t e2 = cudaStreamEndCapture(b->cap, &tmp);
+                if (st != CDV_OK) {
+                    if (tmp) cudaGraphDestroy(tmp);
+                    return st;
+                }
+                BCUDA(e2, "end capture");
+                gr = tmp;
+            } else {
+                st = build_loop_graph(b->cap, batch_phase, &R, &gr);
+            }
             if (st != CDV_OK) return st;
             b->graph = gr;
             BCUDA(cudaGraphInstantiate(&b->gexec, gr, 0), "instantiate graph");
             b->key_y = ky;
             b->key_x = kx;
             b->key_K = K;
+            b->key_persist = persist;
             b->key_o = o;
             b->key_valid = true;
         }
         BCUDA(cudaGraphLaunch(b->gexec, s), "graph launch");
     } else {
         b->key_valid = false;
-        cdv_status st = batch_enqueue(b, K, o, s);
+        cdv_status st = persist ? batch_persist_enqueue(b, K, o, s) : batch_enqueue(b, K, o, s);
         if (st != CDV_OK) return st;
     }
     if (!reports) return CDV_OK;
     BCUDA(cudaStreamSynchronize(s), "batch sync");
+    if (persist) {
+        int flags[2] = {0, 0};
+        BCUDA(cudaMemcpy(flags, b->d_flags, sizeof flags, cudaMemcpyDeviceToHost), "read flags");
+        if (flags[1]) return bfail(CDV_ERR_TIMEOUT, "persistent batched run: a CTA found no tile within the wait budget");
+    }
     for (int i = 0; i < b->count; i++) {
         const cdv_batch::Vol& V = b->v[i];
         IterState st;

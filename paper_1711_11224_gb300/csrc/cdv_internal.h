@@ -139,6 +139,25 @@ cudaError_t launch_batch_finalize(const BatchVolCtx* v, int count, cudaStream_t 
 cudaError_t launch_batch_loop_cond(const BatchVolCtx* v, int count, unsigned long long handle, int max_trials,
                                    cudaStream_t s);
 
+// Persistent batched solver (conv_fp32_persist.cu): every volume's whole run in one launch.
+struct BatchPersist {
+    const ConvBatchVol* fi;      // per volume: initial forward, forward trial, adjoint trial
+    const ConvBatchVol* ft;
+    const ConvBatchVol* at;
+    const BatchVolCtx* ctx;
+    const int* order;            // volumes in scan order (most work first)
+    const int2* ntiles;          // per scan position: forward tiles (x), adjoint tiles (y)
+    unsigned long long* word;    // per scan position: phase (high 32 bits) and next tile (low 32 bits), zero at start
+    int* tiles_done;             // per volume: tiles of the current phase completed, zero at start
+    int* vols_done;              // volumes retired, zero at start
+    int* err;                    // CDV_ERR_TIMEOUT when a CTA found no tile for wait_cycles
+    int count, max_trials;
+    long long wait_cycles;
+};
+cudaError_t conv_fp32_persist_prepare();                 // once per process, outside stream capture
+int conv_fp32_persist_grid(size_t smem);                 // resident CTAs of the kernel (SMs x CTAs per SM)
+cudaError_t conv_fp32_persist_launch(const BatchPersist& P, int grid, size_t smem, cudaStream_t s);
+
 // CUDA graph "prologue -> WHILE(body) -> epilogue": `phase` enqueues phase 0 (prologue), 1 (one trial
 // slot; its last kernel sets the loop condition through the handle) or 2 (epilogue) on a stream.
 typedef cdv_status (*PhaseFn)(void* ctx, int phase, bool loop, unsigned long long handle, cudaStream_t s);

@@ -19,6 +19,7 @@
 #include <algorithm>
 
 #include "cdv_internal.h"
+#include "decide.cuh"
 
 namespace cdv {
 
@@ -118,100 +119,6 @@ cudaError_t launch_sumsq(const float* x, int64_t n, double* out, cudaStream_t s)
 {
     sumsq_kernel<<<1, 512, 0, s>>>(x, n, out);
     return cudaGetLastError();
-}
-
-// Deterministic FP64 sum of n partials by one block: strided per-thread sums
-// in index order, then a fixed shared-memory tree.
-__device__ double block_reduce_fixed(const double* a, int n, double* sh)
-{
-    double s = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s += a[i];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-        __syncthreads();
-    }
-    const double t = sh[0];
-    __syncthreads();
-    return t;
-}
-
-__device__ void decide_body(const IterCtx& c, int nf, int nm, int init, double* sh)
-{
-    IterState* st = c.st;
-    if (st->done) return;
-    const double lambda = st->lambda, sigma = st->sigma;
-    double F = 0.5 * block_reduce_fixed(c.part_f, nf, sh);
-    const double M = init ? 0.0 : block_reduce_fixed(c.part_m, nm, sh);
-    if (lambda != 0.0) F += 0.5 * lambda * block_reduce_fixed(c.part_x, init ? 1 : nm, sh);
-    const double D = (sigma != 0.0 && !init) ? block_reduce_fixed(c.part_a, nm, sh) : 0.0;
-    // the first trial of a step (a fresh gradient) also brought <x_k - x_{k-1}, grad f(x_k) - grad f(x_{k-1})>
-    const bool new_sy = st->bb && !init && st->need_grad && st->accepted >= 1;
-    const double SY = new_sy ? block_reduce_fixed(c.part_sy, nm, sh) : 0.0;
-    if (threadIdx.x != 0) return;
-    if (new_sy) st->sy = SY;
-    if (init) {
-        st->f_cur = F;
-        c.f_hist[0] = F;
-        st->need_grad = 1;
-        if (!isfinite(F)) {
-            st->status = CDV_ERR_NONFINITE;
-            st->done = 1;
-        } else if (st->K <= 0) {
-            st->done = 1;
-        }
-        return;
-    }
-    st->trials += 1;
-    if (st->need_grad) st->adj_convs += 1;
-    st->f_trial = F;
-    st->moved = M;
-    if (M == 0.0) {                       // x_t == x_k: stationary point, the run has converged
-        st->status = CDV_ERR_NOT_DESCENDING;
-        st->done = 1;
-        return;
-    }
-    if (!isfinite(F)) {
-        st->status = CDV_ERR_NONFINITE;
-        st->done = 1;
-        return;
-    }
-    if (F < st->f_cur + sigma * D) {      // f(x_{k+1}) < f(x_k) (+ sigma <grad f, x_{k+1} - x_k>): accept
-        const int a = st->accepted;
-        if (a < st->hist_cap) {
-            c.d_hist[a] = st->delta;
-            c.f_hist[a + 1] = F;
-        }
-        st->accepted = a + 1;
-        st->cur ^= 1;
-        st->f_cur = F;
-        st->halvings = 0;
-        if (st->bb) {                     // next step: <s,s>/<s,v> of (x_k - x_{k-1}, grad f(x_k) - grad f(x_{k-1}))
-            double d = st->delta0;
-            if (a >= 1) {
-                const double dmax = st->delta0 * 1048576.0;
-                d = st->sy > 0.0 ? st->ss_last / st->sy : dmax;
-                d = fmin(fmax(d, st->delta0), dmax);
-            }
-            st->ss_last = M;              // ||x_{k+1} - x_k||^2 for the step after
-            st->delta = d;
-        } else {
-            st->delta = st->delta0;
-        }
-        st->need_grad = 1;
-        if (st->accepted >= st->K) st->done = 1;
-    } else {                              // reject: shorten the step, keep x_k and g_k
-        st->rejected += 1;
-        st->halvings += 1;
-        st->need_grad = 0;
-        if (st->halvings > st->max_halvings || st->rejected > st->max_rejects) {
-            st->status = CDV_ERR_NOT_DESCENDING;
-            st->done = 1;
-        } else {
-            st->delta *= st->beta;
-        }
-    }
 }
 
 __global__ void __launch_bounds__(512) decide_kernel(IterCtx c, int nf, int nm, int init)

@@ -281,7 +281,9 @@ class BatchPlan:
         return self
 
     def iterate(self, Ys, Xs=None, K=100, report=True, **kw):
-        """K accepted steps of Steps 1-3 for every volume; returns (Xs, reports)."""
+        """K accepted steps of Steps 1-3 for every volume; returns (Xs, reports).  path="auto" or
+        "persistent" (default): one persistent launch for the whole run; path="general": common trial
+        slots of batched launches."""
         for Y, s in zip(Ys, self.ny_shapes):
             _need(Y, s, "Y")
         if Xs is None:
@@ -289,7 +291,6 @@ class BatchPlan:
             kw.setdefault("x0", "crop")
         for X, m in zip(Xs, self.ms):
             _need(X, m, "X")
-        kw.pop("path", None)
         o = Plan.opts(**kw)
         reps = None
         hist = []

@@ -1,9 +1,11 @@
 """Batched solver: many uneven volumes with their own templates iterated together.
 
 A volume's iterates do not depend on the tile shape nor on the other volumes,
-so the batched result must equal cdv_iterate on each volume alone, bit for
-bit; cdv_iterate itself is held to the FP64 oracle elsewhere, and here too
-on two small volumes.
+nor on how the run is launched (one persistent launch, the default, or common
+trial slots of batched launches), so the batched result must equal
+cdv_iterate on each volume alone, bit for bit; cdv_iterate itself is held to
+the FP64 oracle elsewhere, and here too on two small volumes and, after 200
+steps, on five volumes of the 64-volume workload.
 """
 import numpy as np
 import pytest
@@ -35,14 +37,15 @@ def _single(P, K, **kw):
         return X.cpu().numpy(), rep
 
 
+@pytest.mark.parametrize("path", ["persistent", "general"])
 @pytest.mark.parametrize("autotune", [True, False])
-def test_batch_equals_single_volume_runs(autotune):
+def test_batch_equals_single_volume_runs(autotune, path):
     from paper_1711_11224_gb300 import BatchPlan
     K = 8
     probs = _problems(SHAPES, K)
     with BatchPlan([P.m for P in probs], [P.p for P in probs], autotune=autotune) as bp:
         bp.set_psfs([_dev(P.H) for P in probs])
-        Xs, reps = bp.iterate([_dev(P.Y) for P in probs], K=K, x0="crop")
+        Xs, reps = bp.iterate([_dev(P.Y) for P in probs], K=K, x0="crop", path=path)
         Xb = [X.cpu().numpy() for X in Xs]
     for P, X, r in zip(probs, Xb, reps):
         Xs_, rs = _single(P, K)
@@ -65,6 +68,7 @@ def test_batch_matches_oracle():
 
 
 def test_batch_graph_replay_and_repeat():
+    """Graph replays, stream launches and both paths, switched back and forth on one plan, agree."""
     from paper_1711_11224_gb300 import BatchPlan
     probs = _problems(SHAPES[:3], 5)
     with BatchPlan([P.m for P in probs], [P.p for P in probs]) as bp:
@@ -72,13 +76,41 @@ def test_batch_graph_replay_and_repeat():
         Ys = [_dev(P.Y) for P in probs]
         Xs = [torch.empty(P.m, device="cuda") for P in probs]
         outs = []
-        for g in (True, True, False):
-            bp.iterate(Ys, Xs, K=5, x0="crop", use_graph=g)
+        for g, path in ((True, "persistent"), (True, "persistent"), (False, "persistent"), (True, "general"),
+                        (False, "general"), (True, "persistent")):
+            bp.iterate(Ys, Xs, K=5, x0="crop", use_graph=g, path=path)
             outs.append([X.cpu().numpy() for X in Xs])
-    for a, b in zip(outs[0], outs[1]):
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            np.testing.assert_array_equal(a, b)
+
+
+def test_batch_backtracking_and_early_stop():
+    """Rejected trials (a first length of 8/L halved back) and volumes that stop at different times
+    (when they exceed max_rejects) in the persistent run, against the slot path."""
+    from paper_1711_11224_gb300 import BatchPlan
+    probs = _problems(SHAPES[:4], 6)
+    res = {}
+    with BatchPlan([P.m for P in probs], [P.p for P in probs]) as bp:
+        bp.set_psfs([_dev(P.H) for P in probs])
+        for path in ("persistent", "general"):
+            Xs, reps = bp.iterate([_dev(P.Y) for P in probs], K=6, x0="crop", delta0=8.0 / max(
+                oracle.lipschitz(P.H) for P in probs), max_rejects=3, path=path)
+            res[path] = ([X.cpu().numpy() for X in Xs], reps)
+    (Xp, rp), (Xg, rg) = res["persistent"], res["general"]
+    assert any(r["rejected"] > 0 for r in rp)
+    for a, b, r1, r2 in zip(Xp, Xg, rp, rg):
         np.testing.assert_array_equal(a, b)
-    for a, b in zip(outs[0], outs[2]):
-        np.testing.assert_array_equal(a, b)
+        assert (r1["accepted"], r1["rejected"], r1["status"]) == (r2["accepted"], r2["rejected"], r2["status"])
+
+
+def test_batch_small_path_rejected():
+    from paper_1711_11224_gb300 import BatchPlan, _binding
+    probs = _problems(SHAPES[:2], 2)
+    with BatchPlan([P.m for P in probs], [P.p for P in probs], autotune=False) as bp:
+        bp.set_psfs([_dev(P.H) for P in probs])
+        with pytest.raises(_binding.CdvError, match="UNSUPPORTED"):
+            bp.iterate([_dev(P.Y) for P in probs], K=2, x0="crop", path="small")
 
 
 @pytest.fixture(scope="module")
