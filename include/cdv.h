@@ -330,6 +330,17 @@ cdv_status cdv_batch_set_psfs(cdv_batch* b, const float* const* H, void* stream)
 cdv_status cdv_batch_iterate(cdv_batch* b, const float* const* Y, float* const* X, int K, const cdv_iter_opts* opts,
                              cdv_iter_report* reports, void* stream);
 
+/*
+ * Budget, in SM clock cycles, for which a CTA of the persistent batched run
+ * may find no tile to take before it records CDV_ERR_TIMEOUT and leaves (the
+ * other CTAs leave at their next look; cdv_batch_iterate with reports then
+ * returns CDV_ERR_TIMEOUT).  0: the default, 1e9 cycles (about 0.5 s), far
+ * longer than any tile or step rule takes.  The paper has no counterpart: this
+ * bounds the persistent kernel's idle loop.  Takes effect at the next call (a
+ * captured graph is re-captured).  Negative cycles: CDV_ERR_INVALID_ARG.
+ */
+cdv_status cdv_batch_set_wait_cycles(cdv_batch* b, long long cycles);
+
 /* Free everything the batch plan owns.  NULL is accepted. */
 cdv_status cdv_batch_destroy(cdv_batch* b);
 

@@ -30,7 +30,7 @@ EXPORTS = [
     "cdv_iter_opts_default", "cdv_iterate", "cdv_iterate_host", "cdv_richardson_lucy", "cdv_plan_sync_status",
     "cdv_grad_psf_static", "cdv_batch_plan_create", "cdv_batch_workspace_size", "cdv_batch_set_psfs",
     "cdv_batch_iterate", "cdv_batch_destroy", "cdv_plan_describe", "cdv_plan_set_psf_factors",
-    "cdv_plan_set_wait_cycles", "cdv_probe_fp32_fma",
+    "cdv_plan_set_wait_cycles", "cdv_probe_fp32_fma", "cdv_batch_set_wait_cycles",
 ]
 
 
@@ -97,6 +97,7 @@ def load(path=LIB_PATH):
     lib.cdv_richardson_lucy.argtypes = [vp, vp, vp, i32, vp]
     lib.cdv_plan_sync_status.argtypes = [vp, vp]
     lib.cdv_plan_set_wait_cycles.argtypes = [vp, ctypes.c_longlong]
+    lib.cdv_batch_set_wait_cycles.argtypes = [vp, ctypes.c_longlong]
     lib.cdv_probe_fp32_fma.argtypes = [vp, i32, i32, i32, vp]
     lib.cdv_grad_psf_static.argtypes = [i32, i64p, ctypes.POINTER(ctypes.c_int32), i32, vp, vp, vp, vp]
     lib.cdv_batch_plan_create.argtypes = [ctypes.POINTER(vp), i32, i32, i64p, ctypes.POINTER(ctypes.c_int32), i32, i32,

@@ -101,6 +101,7 @@ struct cdv_batch {
     int* d_flags = nullptr;             // [0] volumes retired, [1] error
     size_t psmem = 0;
     int pgrid = 0;
+    long long wait_cycles = kTcWaitCycles;
     cudaStream_t cap = nullptr;
     // one stream per template-width group: the groups' launches of a trial slot run side by side
     // (captured as parallel graph branches), joined before the decision
@@ -472,7 +473,7 @@ static cdv_status batch_persist_enqueue(cdv_batch* b, int K, const cdv_iter_opts
     BCUDA(launch_batch_state_init(b->d_ctx, b->count, o.delta0 > 0.0 ? o.delta0 : 0.0, o.beta, o.max_halvings,
                                   o.max_rejects, K, kBatchHist, s), "state");
     BatchPersist P{b->d_fwd_init, b->d_fwd_trial, b->d_adj_trial, b->d_ctx, b->d_order, b->d_ntiles, b->d_word, b->d_tiles_done,
-                   b->d_flags, b->d_flags + 1, b->count, K + o.max_rejects + 1, kTcWaitCycles};
+                   b->d_flags, b->d_flags + 1, b->count, K + o.max_rejects + 1, b->wait_cycles};
     BCUDA(conv_fp32_persist_launch(P, b->pgrid, b->psmem, s), "persistent run");
     BCUDA(launch_batch_finalize(b->d_ctx, b->count, s), "finalize");
     return CDV_OK;
@@ -583,6 +584,15 @@ cdv_status cdv_batch_iterate(cdv_batch* b, const float* const* Y, float* const* 
         if (r.delta_hist && nh > 0)
             BCUDA(cudaMemcpy(r.delta_hist, V.d_hist, nh * sizeof(double), cudaMemcpyDeviceToHost), "read delta");
     }
+    return CDV_OK;
+}
+
+cdv_status cdv_batch_set_wait_cycles(cdv_batch* b, long long cycles)
+{
+    if (!b) return bfail(CDV_ERR_INVALID_ARG, "NULL batch plan");
+    if (cycles < 0) return bfail(CDV_ERR_INVALID_ARG, "cycles = %lld", cycles);
+    b->wait_cycles = cycles == 0 ? kTcWaitCycles : cycles;
+    b->key_valid = false;                  // a captured graph holds the old launch parameters
     return CDV_OK;
 }
 

@@ -280,6 +280,11 @@ class BatchPlan:
         self.H = list(Hs)
         return self
 
+    def set_wait_cycles(self, cycles=0):
+        """Idle budget (SM cycles) of a CTA of the persistent run before it reports CDV_ERR_TIMEOUT
+        (0: the default, about 0.5 s)."""
+        B.check(self.lib.cdv_batch_set_wait_cycles(self._h, int(cycles)))
+
     def iterate(self, Ys, Xs=None, K=100, report=True, **kw):
         """K accepted steps of Steps 1-3 for every volume; returns (Xs, reports).  path="auto" or
         "persistent" (default): one persistent launch for the whole run; path="general": common trial

@@ -9,6 +9,9 @@
   budget of one clock cycle the waits run out, the kernel records
   CDV_ERR_TIMEOUT, drains its own copies and exits, and the plan works again
   once the status has been read and the budget restored.
+* Idle budget of the persistent batched run: with one clock cycle a CTA that
+  finds no tile at once records CDV_ERR_TIMEOUT, every CTA leaves, the call
+  reports it, and the next run with the default budget is exact.
 """
 import numpy as np
 import pytest
@@ -98,3 +101,25 @@ def test_tc_iterate_timeout_reported_then_cleared():
     ref = oracle.iterate(P.Y, P.H, oracle.x0_crop(P.Y, P.p), 4)
     assert rep["status"] == "CDV_OK" and rep["accepted"] == 4
     assert rel_l2(Xg, ref["X"]) <= 1e-4
+
+
+def test_batch_persistent_idle_budget_runs_out_and_recovers():
+    """A one-cycle idle budget: CTAs that find no tile at once record CDV_ERR_TIMEOUT and every CTA
+    leaves; the call reports it, and the next run with the default budget is exact again."""
+    from paper_1711_11224_gb300 import BatchPlan, CdvError
+    probs = [synth.scaled_fil3d(m, q, seed=i, K=3) for i, (m, q) in
+             enumerate([((8, 40, 33), (3, 5, 7)), ((12, 30, 40), (5, 5, 7))])]
+    with BatchPlan([P.m for P in probs], [P.p for P in probs], autotune=False) as bp:
+        bp.set_psfs([_dev(P.H) for P in probs])
+        Ys = [_dev(P.Y) for P in probs]
+        bp.set_wait_cycles(1)
+        with pytest.raises(CdvError) as ei:
+            bp.iterate(Ys, K=3, x0="crop")
+        assert ei.value.status == TIMEOUT
+        bp.set_wait_cycles(0)
+        Xs, reps = bp.iterate(Ys, K=3, x0="crop")
+        Xb = [X.cpu().numpy() for X in Xs]
+        Xs2, _ = bp.iterate(Ys, K=3, x0="crop", path="general")
+        for a, X in zip(Xb, Xs2):
+            np.testing.assert_array_equal(a, X.cpu().numpy())
+    assert all(r["status"] == "CDV_OK" and r["accepted"] == 3 for r in reps)
