@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(512) grad_psf_q_kernel(GradPsfPlan g, int RS, 
                                                          const float* dY, double* partial)
 {
     constexpr int DP = QLayout<Q3>::DP;
-    constexpr int NW = (Q3 + 3 + 3) / 4;                    // 16-byte loads of one dY window
+    constexpr int NW8 = (Q3 + 7 + 3) / 4;                   // 16-byte loads of one dY window of 8 columns
     extern __shared__ __align__(16) float smq[];
     const int q2 = g.q2, drows = QTR + q2 - 1, npair = (q2 + 1) / 2;
     const int buf = QTR * QXP + drows * DP;                 // floats per buffer
@@ -255,37 +255,28 @@ __global__ void __launch_bounds__(512) grad_psf_q_kernel(GradPsfPlan g, int RS, 
                 const float* xr = sx + rr * QXP;
                 const float* da = sd + (rr + j2a) * DP;
                 const float* db = sd + (rr + j2b) * DP;
-#pragma unroll 2
-                for (int kb = 0; kb < QKW; kb += 4) {
-                    const float4 x4 = *reinterpret_cast<const float4*>(xr + kb);
-                    float wa[4 * NW], wb[4 * NW];
+                // 8 columns per step (two x loads and NW8 loads of each dY window for 16 Q3 FMAs), columns
+                // in ascending order as four at a time would take them
+#pragma unroll 1
+                for (int kb = 0; kb < QKW; kb += 8) {
+                    const float4 x0 = *reinterpret_cast<const float4*>(xr + kb);
+                    const float4 x1 = *reinterpret_cast<const float4*>(xr + kb + 4);
+                    const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+                    float wa[4 * NW8], wb[4 * NW8];
 #pragma unroll
-                    for (int i = 0; i < NW; i++) {
+                    for (int i = 0; i < NW8; i++) {
                         const float4 a = *reinterpret_cast<const float4*>(da + kb + 4 * i);
                         const float4 c = *reinterpret_cast<const float4*>(db + kb + 4 * i);
                         wa[4 * i] = a.x; wa[4 * i + 1] = a.y; wa[4 * i + 2] = a.z; wa[4 * i + 3] = a.w;
                         wb[4 * i] = c.x; wb[4 * i + 1] = c.y; wb[4 * i + 2] = c.z; wb[4 * i + 3] = c.w;
                     }
 #pragma unroll
-                    for (int q = 0; q < Q3; q++) {
-                        acc[0][q] = fmaf(x4.x, wa[q], acc[0][q]);
-                        acc[1][q] = fmaf(x4.x, wb[q], acc[1][q]);
-                    }
+                    for (int e = 0; e < 8; e++)
 #pragma unroll
-                    for (int q = 0; q < Q3; q++) {
-                        acc[0][q] = fmaf(x4.y, wa[q + 1], acc[0][q]);
-                        acc[1][q] = fmaf(x4.y, wb[q + 1], acc[1][q]);
-                    }
-#pragma unroll
-                    for (int q = 0; q < Q3; q++) {
-                        acc[0][q] = fmaf(x4.z, wa[q + 2], acc[0][q]);
-                        acc[1][q] = fmaf(x4.z, wb[q + 2], acc[1][q]);
-                    }
-#pragma unroll
-                    for (int q = 0; q < Q3; q++) {
-                        acc[0][q] = fmaf(x4.w, wa[q + 3], acc[0][q]);
-                        acc[1][q] = fmaf(x4.w, wb[q + 3], acc[1][q]);
-                    }
+                        for (int q = 0; q < Q3; q++) {
+                            acc[0][q] = fmaf(xv[e], wa[q + e], acc[0][q]);
+                            acc[1][q] = fmaf(xv[e], wb[q + e], acc[1][q]);
+                        }
                 }
             }
             if (++nacc == flush || t + g.chunks >= ntiles) {
