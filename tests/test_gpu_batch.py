@@ -152,3 +152,13 @@ def test_batch64_volumes_match_oracle_200_steps(batch64_run):
         print("volume %d m=%s q=%s: x_200 rel-L2 %.3e" % (i, P.m, P.H.shape, e))
         assert e <= TOL_ITER
         np.testing.assert_allclose(reps[i]["f"], ref["f"], rtol=1e-5)
+
+
+def test_single_plan_rejects_the_persistent_path():
+    """CDV_PATH_PERSISTENT belongs to the batched solver; cdv_iterate answers CDV_ERR_UNSUPPORTED."""
+    from paper_1711_11224_gb300 import Plan, _binding
+    P = _problems(SHAPES[:1], 2)[0]
+    with Plan(P.m, P.p) as pl:
+        pl.set_psf(_dev(P.H))
+        with pytest.raises(_binding.CdvError, match="UNSUPPORTED"):
+            pl.iterate(_dev(P.Y), K=2, x0="crop", path="persistent")
