@@ -772,11 +772,12 @@ def run_batch(args):
            "iters_per_s": acc / t, "gpu_launches": launches,
            "run": "one persistent launch for every volume's whole run (cdv_batch_iterate, path persistent)",
            "slot_path": {"value": sum(r["gmac"] for r in reps_slot) / t_slot, "unit": "GMAC/s", "seconds": t_slot,
-                         "gpu_launches": launches_slot,
+                         "gpu_launches": launches_slot, "speedup_vs_sequential": None,
                          "call": "cdv_batch_iterate, path general: common trial slots of batched launches"},
            "sequential_plain": {"value": sum(r["gmac"] for r in reps) / seq, "unit": "GMAC/s", "seconds": seq,
                                 "call": "cdv_iterate per volume (general path), back to back"},
            "batched_speedup": seq / t, "convolutions": nconv, "clocks": clk.summary()}
+    out["slot_path"]["speedup_vs_sequential"] = seq / t_slot
     bp.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
