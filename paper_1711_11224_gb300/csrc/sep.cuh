@@ -353,25 +353,33 @@ __global__ void __launch_bounds__(kSepThreads) sep_cols_kernel(const SepPass P)
             const int64_t tt = tb + k;
             v[k] = (on && tt >= 0 && tt < kin) ? base[tt * inner] : 0.f;
         }
-        for (int64_t s = sb; s < se; s += C) {
-            // v[Q - 1 ..] from input sample ts on; the pointer walks the pass axis and is dereferenced
-            // only inside [0, kin)
+        // the C input samples of a step are loaded one step ahead (into nx), so that their latency
+        // overlaps the previous step's FMAs; the pointer walks the pass axis and is dereferenced only
+        // inside [0, kin) (off lanes read column 0)
+        float nx[C];
+        auto load_step = [&](int64_t s) {
             const int64_t ts = s + P.o;
             const float* lp = base + ts * inner;
-            if (ts >= 0 && ts + C <= kin) {                  // inside the input (off lanes read column 0)
+            if (ts >= 0 && ts + C <= kin) {
 #pragma unroll
-                for (int k = Q - 1; k < WN; k++) {
-                    v[k] = *lp;
+                for (int c = 0; c < C; c++) {
+                    nx[c] = *lp;
                     lp += inner;
                 }
             } else {
 #pragma unroll
-                for (int k = Q - 1; k < WN; k++) {
-                    const int64_t tt = ts + (k - (Q - 1));
-                    v[k] = (on && tt >= 0 && tt < kin) ? *lp : 0.f;
+                for (int c = 0; c < C; c++) {
+                    const int64_t tt = ts + c;
+                    nx[c] = (on && tt >= 0 && tt < kin) ? *lp : 0.f;
                     lp += inner;
                 }
             }
+        };
+        if (sb < se) load_step(sb);
+        for (int64_t s = sb; s < se; s += C) {
+#pragma unroll
+            for (int c = 0; c < C; c++) v[Q - 1 + c] = nx[c];
+            if (s + C < se) load_step(s + C);
             float acc[C];
 #pragma unroll
             for (int c = 0; c < C; c++) acc[c] = 0.f;
