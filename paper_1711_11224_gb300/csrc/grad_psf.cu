@@ -138,10 +138,12 @@ __global__ void __launch_bounds__(1024) grad_psf_kernel(GradPsfPlan g, GLayout l
 
 // Narrow templates (q3 <= 15): a register-blocked form with double-buffered 16-byte staging.
 //  * CTA (j1, ch) walks tiles (volume, plane k1, rows k2 .. k2 + 15, columns k3 .. k3 + 63);
-//    thread (j2 pair, rs) owns all Q3 outputs dH(j1, j2, .) of two template rows j2 for the tile rows
+//    thread (jp, rs) owns all Q3 outputs dH(j1, j2, .) of template rows j2 = jp and jp + ceil(q2 / 2)
+//    (so the dY rows that the threads of a quarter warp read lie within 8 consecutive rows: no bank
+//    conflicts, where rows 2 jp and 2 jp + 1 put rows 8 apart on the same banks) for the tile rows
 //    rs, rs + RS, ...
-//  * Per 4 columns of a row: one 16-byte load of x, 2 ceil((Q3 + 3) / 4) of the dY rows k2 + j2, and
-//    8 Q3 FMAs (Q3 + 3 window values against 4 x values, for both rows j2).
+//  * Per 8 columns of a row: two 16-byte loads of x, 2 ceil((Q3 + 7) / 4) of the dY rows k2 + j2, and
+//    16 Q3 FMAs (Q3 + 7 window values against 8 x values, for both rows j2).
 //  * The next tile is copied (cp.async) while the current one is summed; sums are FP32 over as many
 //    tiles as keep them at 1024 terms per thread at most, then added into FP64 sums (shared memory),
 //    which are reduced over rs in a fixed order.
@@ -177,7 +179,7 @@ __global__ void __launch_bounds__(512) grad_psf_q_kernel(GradPsfPlan g, int RS, 
     const int j1 = blockIdx.x / g.chunks, ch = blockIdx.x % g.chunks;
     const int tid = threadIdx.x, nthr = npair * RS;
     const int jp = tid % npair, rs = tid / npair;
-    const int j2a = 2 * jp, j2b = min(2 * jp + 1, q2 - 1);  // a lone last row is summed twice, kept once
+    const int j2a = jp, j2b = min(jp + npair, q2 - 1);      // a lone last row is summed twice, kept once
     const bool active = tid < nthr;
     const int64_t n2 = g.m2 + g.q2 - 1, n3 = g.m3 + Q3 - 1, n1 = g.m1 + g.q1 - 1;
     const int64_t t2 = (g.m2 + QTR - 1) / QTR, t3 = (g.m3 + QKW - 1) / QKW;
@@ -296,7 +298,7 @@ __global__ void __launch_bounds__(512) grad_psf_q_kernel(GradPsfPlan g, int RS, 
     __syncthreads();
     if (active && rs == 0) {
         for (int h = 0; h < 2; h++) {
-            const int j2 = h ? 2 * jp + 1 : 2 * jp;
+            const int j2 = h ? jp + npair : jp;
             if (j2 >= q2) continue;
             for (int q = 0; q < Q3; q++) {
                 double sum = 0.0;
