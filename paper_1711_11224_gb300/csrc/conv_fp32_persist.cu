@@ -6,14 +6,15 @@
 // tiles of that direction; the CTAs of the launch take tiles from any volume whose current phase has
 // tiles left, through one 64-bit word per volume (phase in the high half, next tile in the low half,
 // taken with atomicAdd, so a tile index always comes with the phase it belongs to; warp 0 of a CTA
-// scans 32 of these words per load).  The CTA that
-// completes a phase's last tile runs that volume's step rule (after a forward: the FP64 decision of
-// Step 2, in the fixed order of the 512-thread decision kernel) and opens the next phase, or retires
-// the volume.  No CTA waits for another CTA's result: a CTA without a tile to take scans again after
-// a short sleep, so the launch needs no co-residency and cannot deadlock; a CTA that finds no tile for
-// the plan's wait budget records CDV_ERR_TIMEOUT and leaves.  Every tile writes its FP64 partials at
-// its own index, and the decisions sum them in the same order as the per-slot launches, so each
-// volume's iterates equal those of the per-slot batched solver and of cdv_iterate on it alone.
+// scans 32 of these words per load).  The CTA that completes a phase's last tile runs that volume's
+// step rule (after a forward: the FP64 decision of Step 2, in the fixed order of the 512-thread
+// decision kernel) and opens the next phase, or retires the volume.  No CTA waits for another CTA's
+// result: a CTA without a tile to take scans again after a short sleep, so the launch needs no
+// co-residency and cannot deadlock; a CTA that finds no tile for the batch plan's idle budget
+// (cdv_batch_set_wait_cycles) records CDV_ERR_TIMEOUT, and every CTA leaves at its next look.  Every
+// tile writes its FP64 partials at its own index, and the decisions sum them in the same order as the
+// per-slot launches, so each volume's iterates equal those of the per-slot batched solver and of
+// cdv_iterate on it alone.
 #include <algorithm>
 
 #include "conv_fp32.cuh"
