@@ -89,7 +89,11 @@ int cdv_version(void);
  * output-plane slots, for BF16 forms with q1 <= 31 and q3 = 1 mod 4).  The
  * environment variable CDV_TC_KERNEL, read here, overrides the choice:
  * "wide", "narrow", "narrow_rows" or "narrow_flat" (the narrow kernel with the
- * forward's tiles over rows only, or over column groups and rows).
+ * forward's tiles over rows only, or over column groups and rows), and
+ * CDV_TC_DEAL = "free" or "chunks" restricts how the narrow kernel's tile
+ * lists are cut (free cuts per M block, or chunk-major; default: the model's
+ * choice per direction).  Both are measurement aids; the results do not
+ * depend on them.
  */
 cdv_status cdv_plan_create(cdv_plan** out, int n, const int64_t* m, const int32_t* p,
                            cdv_mode mode, void* stream);
